@@ -1,0 +1,164 @@
+/*
+ * mbl.h -- C ABI of the GB300 (sm_103a) library for the matrix-free MBL eigensolver:
+ * interior eigenpairs of the disordered Heisenberg chain restricted to one S^z sector.
+ *
+ * Model (Sec. 2.1, Eq. (model) and Eq. (Hmatrix)), with an anisotropy delta on the
+ * Z_iZ_j part (delta = 1 is the paper's isotropic model):
+ *     H = sum_bonds [ (X_iX_j + Y_iY_j)/4 + delta Z_iZ_j/4 ] + sum_i h_i Z_i/2
+ * Bonds are (i, i+1), i = 0..L-2, plus (L-1, 0) on a periodic chain with L > 2.
+ * Basis: the L-bit words s with popcount n_up (bit i = site i, 1 = spin up), in
+ * ascending integer order; the sector dimension is n = C(L, n_up) (Sec. 2.1, Table 1).
+ * Matrix elements: diagonal d(s) = sum_bonds delta/4 z_i z_j + sum_i h_i/2 z_i
+ * (z = +1 up, -1 down); off-diagonal 1/2 between s and s with the two differing
+ * spins of one bond exchanged.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an int status (MBL_OK = 0, negative on error) and never
+ *     throw.  Arguments are validated before any launch; on MBL_ERR_ARG nothing is
+ *     enqueued.
+ *   - "_dev" pointers are device pointers owned by the caller; "_host" pointers are
+ *     host memory owned by the caller.  The library allocates no device memory: the
+ *     solvers take a caller-owned workspace sized by the matching *_workspace_size.
+ *   - Work is enqueued on the caller's stream (mbl_stream_t is cudaStream_t; NULL is
+ *     the legacy default stream).  Entry points that return host results (the
+ *     solvers) synchronise that stream before returning; the others do not.
+ *   - Blocks of vectors are row-major n x k with a leading dimension ld >= k
+ *     (element (r, c) at ptr[r * ld + c]).
+ */
+#ifndef MBL_H
+#define MBL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mbl_stream_t; /* identical to cudaStream_t */
+
+/* status codes */
+#define MBL_OK 0
+#define MBL_ERR_ARG -1            /* invalid argument; nothing was launched */
+#define MBL_ERR_WORKSPACE -2      /* workspace smaller than *_workspace_size reported */
+#define MBL_ERR_CUDA -3           /* a CUDA runtime call or launch failed */
+#define MBL_ERR_NOT_CONVERGED -4  /* max_iter reached; outputs hold the best estimates */
+#define MBL_ERR_BREAKDOWN -5      /* orthonormalisation lost rank beyond recovery */
+#define MBL_ERR_NUMERIC -6        /* NaN or Inf met in a residual or Gram matrix */
+
+#define MBL_F32 0
+#define MBL_F64 1
+
+#define MBL_MODE_FP64 0  /* every step in FP64 */
+#define MBL_MODE_MIXED 1 /* FP32 preconditioner and FP32 Gram matrices; FP64 products
+                            of H for X, W, P, FP64 Rayleigh-Ritz, orthonormalisation of
+                            X and residuals (Sec. 6.2: PCG in single, LOBPCG in double) */
+
+/* Human-readable text for a status code (static storage). */
+const char *mbl_status_string(int status);
+
+/* One disorder realisation of the chain.  h_host: L FP64 fields (host memory, read
+ * during the call only).  Requirements: 2 <= L <= 32, 0 <= n_up <= L, finite h and
+ * delta. */
+typedef struct {
+    int L;
+    int n_up;
+    int periodic; /* 0 = open chain (the paper's choice), 1 = periodic */
+    double delta;
+    const double *h_host;
+} mbl_chain;
+
+/* ---- basis (Sec. 2.1 sector block-diagonalisation; Table 1) ---------------------- */
+
+/* n = C(L, n_up), or -1 when 1 <= L <= 32 and 0 <= n_up <= L do not hold. */
+int64_t mbl_basis_size(int L, int n_up);
+
+/* states_dev[r] = the r-th L-bit word with popcount n_up in ascending order, for
+ * r = 0..n-1 (combinatorial-number-system unranking).  n must equal
+ * mbl_basis_size(L, n_up).  states_dev: n uint32 words. */
+int mbl_basis_build(int L, int n_up, uint32_t *states_dev, int64_t n, mbl_stream_t stream);
+
+/* ranks_dev[q] = position of words_dev[q] in that list (sum over up spins of
+ * C(position, index)), or -1 when the word is not in the sector (wrong popcount or
+ * bits at or above L).  cnt words in, cnt int64 out. */
+int mbl_basis_rank(int L, int n_up, const uint32_t *words_dev, int64_t *ranks_dev, int64_t cnt,
+                   mbl_stream_t stream);
+
+/* ---- Hamiltonian product (Sec. 4.1, the MATVEC) ---------------------------------- */
+
+/* Y = (H - sigma I) X on the sector, X and Y row-major n x k blocks (n = C(L, n_up))
+ * with leading dimensions ldx, ldy >= k, element type dtype (MBL_F32 or MBL_F64,
+ * accumulation in the same type).  Gather form: every output row is written once by
+ * one thread group, no atomics, so results are bitwise reproducible.  X and Y must
+ * not overlap.  Requires 1 <= k <= 256. */
+int mbl_hamiltonian_apply(const mbl_chain *chain, double sigma, int dtype, const void *X_dev,
+                          int64_t ldx, void *Y_dev, int64_t ldy, int64_t n, int k,
+                          mbl_stream_t stream);
+
+/* ---- folded-spectrum LOBPCG (Sec. 3.2, Sec. 6.2) ---------------------------------- */
+
+typedef struct {
+    int nev;        /* wanted eigenpairs nearest sigma, 1 <= nev <= k */
+    int k;          /* block width, nev <= k <= 64, 3k <= n */
+    int max_iter;   /* LOBPCG iterations before MBL_ERR_NOT_CONVERGED */
+    int pcg_iters;  /* Jacobi-PCG steps per LOBPCG iteration (the preconditioner) */
+    double tol;     /* accept when ||H y - lambda y||_2 <= tol * norm_h for all nev pairs */
+    double pcg_tol; /* 0: always pcg_iters steps; > 0: freeze a column once
+                       r^T M^-1 r <= pcg_tol^2 times its initial value */
+    double norm_h;  /* scale of the tolerance; <= 0: a Gershgorin bound max_s |d(s)| + f(s)/2 */
+    int mode;       /* MBL_MODE_FP64 or MBL_MODE_MIXED */
+    int use_graph;  /* 1: capture the body of an iteration once as a CUDA graph and replay it */
+    int timing;     /* 1: record CUDA events between the phases of every iteration and report
+                       the per-phase device time in mbl_lobpcg_stats (disables use_graph) */
+} mbl_lobpcg_opts;
+
+typedef struct {
+    int iters;            /* LOBPCG iterations taken */
+    int converged;        /* 1 when every wanted pair met the tolerance */
+    int64_t matvecs;      /* single-column applications of H (a block of k counts k) */
+    double seconds;       /* wall time of the call */
+    double max_rel_resid; /* max over the returned pairs of ||Hy - lambda y|| / norm_h */
+    double norm_h;        /* the norm the tolerance was scaled by */
+    /* device seconds per phase when opts->timing = 1 (else 0): setup (preconditioner
+       diagonal, start block), residual block R, Jacobi-PCG sweeps, orthogonalisation of
+       W and P with their products, Gram matrices of S, small dense steps (SVQB,
+       Rayleigh-Ritz), block updates with Cholesky-QR, products of the new block, and the
+       H Rayleigh-Ritz convergence test */
+    double t_setup, t_resid, t_pcg, t_wp, t_gram, t_small, t_update, t_refresh, t_hrr;
+} mbl_lobpcg_stats;
+
+/* Bytes of device workspace mbl_lobpcg_solve needs for this chain and options. */
+int mbl_lobpcg_workspace_size(const mbl_chain *chain, const mbl_lobpcg_opts *opts,
+                              size_t *bytes);
+
+/* The opts->nev eigenpairs of H nearest sigma, by LOBPCG on A = (H - sigma I)^2 with a
+ * column-wise Jacobi-PCG preconditioner (M = diag(A) = (d - sigma)^2 + f/4).  Every
+ * iteration a Rayleigh-Ritz with H on span(X) gives the Ritz pairs whose residuals
+ * decide convergence; the same step is the final extraction.
+ *   X0_dev:    n x k FP64 starting block, row-major, ld = k (read only).
+ *   workspace: >= mbl_lobpcg_workspace_size bytes of device memory, 256-byte aligned.
+ *   evals_host: nev FP64, ascending.  evecs_dev: n x nev FP64, row-major, ld = nev,
+ *   unit columns.  resid_host: nev FP64 absolute residual norms ||Hy - lambda y||_2
+ *   (each may be NULL).  stats: may be NULL.
+ * Returns MBL_OK, or MBL_ERR_NOT_CONVERGED with the current estimates written. */
+int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
+                     const double *X0_dev, void *workspace_dev, size_t workspace_bytes,
+                     double *evals_host, double *evecs_dev, double *resid_host,
+                     mbl_lobpcg_stats *stats, mbl_stream_t stream);
+
+/* Spectrum bounds E_min, E_max of the sector Hamiltonian (used to place sigma at the
+ * middle of the spectrum and to scale tolerances): unpreconditioned LOBPCG on +H and
+ * on -H, block width k (2 <= k <= 16), stopping when the lowest Ritz pair has
+ * ||B x - theta x|| <= tol |theta|.  X0_dev: n x k FP64 start block (ld = k).
+ * Workspace: mbl_bounds_workspace_size bytes. */
+int mbl_bounds_workspace_size(const mbl_chain *chain, int k, size_t *bytes);
+int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, int max_iter,
+                        const double *X0_dev, void *workspace_dev, size_t workspace_bytes,
+                        double *emin_host, double *emax_host, int *iters_host,
+                        mbl_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBL_H */

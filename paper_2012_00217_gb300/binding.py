@@ -1,0 +1,228 @@
+"""Thin ctypes binding of the C ABI in include/mbl.h (argument marshalling only).
+
+Every function has the same name as its C entry point without the ``mbl_`` prefix.
+Device buffers are torch CUDA tensors (passed by data pointer); the stream is
+torch's current stream on the tensors' device.  Nothing here computes any part of
+the method: it checks shapes and dtypes, forwards pointers and sizes, and raises
+``MBLError`` on a non-zero status.  Loading fails loudly when the library has not
+been built (there is no CPU fallback).
+"""
+import ctypes
+import functools
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmbl_gb300.so")
+
+MBL_OK = 0
+MBL_ERR_ARG = -1
+MBL_ERR_WORKSPACE = -2
+MBL_ERR_CUDA = -3
+MBL_ERR_NOT_CONVERGED = -4
+MBL_ERR_BREAKDOWN = -5
+MBL_ERR_NUMERIC = -6
+MBL_F32 = 0
+MBL_F64 = 1
+MODE_FP64 = 0
+MODE_MIXED = 1
+
+EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis_rank",
+            "mbl_hamiltonian_apply", "mbl_lobpcg_workspace_size", "mbl_lobpcg_solve",
+            "mbl_bounds_workspace_size", "mbl_spectrum_bounds")
+
+
+class MBLError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, status_string(status), status))
+
+
+class Chain(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("n_up", ctypes.c_int), ("periodic", ctypes.c_int),
+                ("delta", ctypes.c_double), ("h_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class LobpcgOpts(ctypes.Structure):
+    _fields_ = [("nev", ctypes.c_int), ("k", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("pcg_iters", ctypes.c_int), ("tol", ctypes.c_double), ("pcg_tol", ctypes.c_double),
+                ("norm_h", ctypes.c_double), ("mode", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+class LobpcgStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("matvecs", ctypes.c_int64),
+                ("seconds", ctypes.c_double), ("max_rel_resid", ctypes.c_double),
+                ("norm_h", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_resid", ctypes.c_double),
+                ("t_pcg", ctypes.c_double), ("t_wp", ctypes.c_double), ("t_gram", ctypes.c_double),
+                ("t_small", ctypes.c_double), ("t_update", ctypes.c_double), ("t_refresh", ctypes.c_double),
+                ("t_hrr", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+@functools.lru_cache(maxsize=1)
+def lib():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("CUDA library %s is not built; run __graft_entry__.build()" % LIB_PATH)
+    so = ctypes.CDLL(LIB_PATH)
+    p, i32, i64, f64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    pch = ctypes.POINTER(Chain)
+    popt = ctypes.POINTER(LobpcgOpts)
+    so.mbl_status_string.restype = ctypes.c_char_p
+    so.mbl_status_string.argtypes = [i32]
+    so.mbl_basis_size.restype = i64
+    so.mbl_basis_size.argtypes = [i32, i32]
+    so.mbl_basis_build.restype = i32
+    so.mbl_basis_build.argtypes = [i32, i32, p, i64, p]
+    so.mbl_basis_rank.restype = i32
+    so.mbl_basis_rank.argtypes = [i32, i32, p, p, i64, p]
+    so.mbl_hamiltonian_apply.restype = i32
+    so.mbl_hamiltonian_apply.argtypes = [pch, f64, i32, p, i64, p, i64, i64, i32, p]
+    so.mbl_lobpcg_workspace_size.restype = i32
+    so.mbl_lobpcg_workspace_size.argtypes = [pch, popt, ctypes.POINTER(sz)]
+    so.mbl_lobpcg_solve.restype = i32
+    so.mbl_lobpcg_solve.argtypes = [pch, f64, popt, p, p, sz, p, p, p, ctypes.POINTER(LobpcgStats), p]
+    so.mbl_bounds_workspace_size.restype = i32
+    so.mbl_bounds_workspace_size.argtypes = [pch, i32, ctypes.POINTER(sz)]
+    so.mbl_spectrum_bounds.restype = i32
+    so.mbl_spectrum_bounds.argtypes = [pch, i32, f64, i32, p, p, sz, p, p, p, p]
+    return so
+
+
+def status_string(status):
+    return lib().mbl_status_string(int(status)).decode()
+
+
+def _check(rc, what, ok=(MBL_OK,)):
+    if rc not in ok:
+        raise MBLError(rc, what)
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(t):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _dev(t, dtype, what):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s" % (what, dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_chain(L, h, delta=1.0, periodic=False, n_up=None):
+    """Marshal one disorder realisation into the C struct (h copied to a host array
+    kept alive on the returned object)."""
+    hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+    c = Chain(int(L), int(L) // 2 if n_up is None else int(n_up), int(bool(periodic)), float(delta),
+              hh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    c._keep = hh
+    return c
+
+
+def basis_size(L, n_up):
+    return int(lib().mbl_basis_size(int(L), int(n_up)))
+
+
+def basis_build(L, n_up, states):
+    """states: int32/uint32-sized CUDA tensor (torch.int32) of basis_size(L, n_up) entries."""
+    torch = _torch()
+    ptr = _dev(states, torch.int32, "states")
+    _check(lib().mbl_basis_build(int(L), int(n_up), ptr, states.numel(), _stream_ptr(states)),
+           "mbl_basis_build")
+    return states
+
+
+def basis_rank(L, n_up, words, ranks):
+    torch = _torch()
+    wp = _dev(words, torch.int32, "words")
+    rp = _dev(ranks, torch.int64, "ranks")
+    if words.numel() != ranks.numel():
+        raise ValueError("words and ranks differ in size")
+    _check(lib().mbl_basis_rank(int(L), int(n_up), wp, rp, words.numel(), _stream_ptr(words)),
+           "mbl_basis_rank")
+    return ranks
+
+
+def hamiltonian_apply(chain, sigma, X, Y):
+    """Y = (H - sigma I) X for 2-D CUDA tensors (float32 or float64, row stride >= k,
+    unit column stride)."""
+    torch = _torch()
+    if X.dim() != 2 or Y.dim() != 2 or X.shape != Y.shape:
+        raise ValueError("X and Y must be 2-D with equal shapes")
+    if X.dtype != Y.dtype or X.dtype not in (torch.float32, torch.float64):
+        raise TypeError("X and Y must both be float32 or float64")
+    if X.stride(1) != 1 or Y.stride(1) != 1:
+        raise ValueError("columns must be contiguous")
+    dt = MBL_F32 if X.dtype == torch.float32 else MBL_F64
+    n, k = X.shape
+    _check(lib().mbl_hamiltonian_apply(ctypes.byref(chain), float(sigma), dt, _dev(X, X.dtype, "X"),
+                                       X.stride(0), _dev(Y, Y.dtype, "Y"), Y.stride(0), n, k,
+                                       _stream_ptr(X)), "mbl_hamiltonian_apply")
+    return Y
+
+
+def make_opts(nev, k, tol=1e-8, max_iter=200, pcg_iters=50, pcg_tol=0.0, norm_h=0.0,
+              mode=MODE_MIXED, use_graph=1, timing=0):
+    return LobpcgOpts(int(nev), int(k), int(max_iter), int(pcg_iters), float(tol), float(pcg_tol),
+                      float(norm_h), int(mode), int(use_graph), int(timing))
+
+
+def lobpcg_workspace_size(chain, opts):
+    out = ctypes.c_size_t(0)
+    _check(lib().mbl_lobpcg_workspace_size(ctypes.byref(chain), ctypes.byref(opts), ctypes.byref(out)),
+           "mbl_lobpcg_workspace_size")
+    return int(out.value)
+
+
+def lobpcg_solve(chain, sigma, opts, X0, workspace, evecs=None, allow_not_converged=False):
+    """Returns (evals ndarray, resid ndarray, stats dict, status).  X0: n x k float64 CUDA
+    tensor; workspace: uint8 CUDA tensor of >= lobpcg_workspace_size bytes; evecs:
+    optional n x nev float64 CUDA tensor."""
+    torch = _torch()
+    nev = opts.nev
+    evals = np.zeros(nev, dtype=np.float64)
+    resid = np.zeros(nev, dtype=np.float64)
+    stats = LobpcgStats()
+    ev_ptr = _dev(evecs, torch.float64, "evecs") if evecs is not None else None
+    if evecs is not None and (evecs.shape != (X0.shape[0], nev) or not evecs.is_contiguous()):
+        raise ValueError("evecs must be a contiguous n x nev tensor")
+    if not X0.is_contiguous() or X0.dim() != 2 or X0.shape[1] != opts.k:
+        raise ValueError("X0 must be a contiguous n x k tensor")
+    ok = (MBL_OK, MBL_ERR_NOT_CONVERGED) if allow_not_converged else (MBL_OK,)
+    rc = lib().mbl_lobpcg_solve(ctypes.byref(chain), float(sigma), ctypes.byref(opts),
+                                _dev(X0, torch.float64, "X0"), _dev(workspace, torch.uint8, "workspace"),
+                                workspace.numel(), evals.ctypes.data_as(ctypes.c_void_p), ev_ptr,
+                                resid.ctypes.data_as(ctypes.c_void_p), ctypes.byref(stats),
+                                _stream_ptr(X0))
+    _check(rc, "mbl_lobpcg_solve", ok)
+    return evals, resid, stats.as_dict(), rc
+
+
+def bounds_workspace_size(chain, k):
+    out = ctypes.c_size_t(0)
+    _check(lib().mbl_bounds_workspace_size(ctypes.byref(chain), int(k), ctypes.byref(out)),
+           "mbl_bounds_workspace_size")
+    return int(out.value)
+
+
+def spectrum_bounds(chain, X0, workspace, tol=1e-10, max_iter=500):
+    """(E_min, E_max, iterations) by LOBPCG on +H and -H from the n x k block X0."""
+    torch = _torch()
+    emin, emax, iters = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().mbl_spectrum_bounds(ctypes.byref(chain), X0.shape[1], float(tol), int(max_iter),
+                                     _dev(X0, torch.float64, "X0"), _dev(workspace, torch.uint8, "workspace"),
+                                     workspace.numel(), ctypes.byref(emin), ctypes.byref(emax),
+                                     ctypes.byref(iters), _stream_ptr(X0)), "mbl_spectrum_bounds")
+    return emin.value, emax.value, iters.value

@@ -1,0 +1,908 @@
+// mbl_apply.cu -- the block product Y = (H - sigma I) X on one S^z sector (Sec. 4.1,
+// the MATVEC that dominates the solver's cost, Sec. 3.2) and the Jacobi-PCG kernels
+// built around it (Sec. 3.2 preconditioner; Sec. 6.2 runs it in single precision).
+//
+// Gather (pull) form: each output row is produced by one group of lanes that reads
+// its own row of X and the rows of its flip-flop neighbours, so no atomics are
+// needed and results are bitwise reproducible.  Index arithmetic uses the
+// combinatorial number system: exchanging the spins of open bond (i, i+1) moves the
+// rank by +C(i, c) (up spin moves right) or -C(i, c) (moves left), c = number of up
+// spins below site i; the wrap bond of a periodic chain is re-ranked.
+//
+// Work split inside a warp (k wide enough for several lanes per row): every lane
+// first ranks one of 32 consecutive rows (state, diagonal, neighbour list into
+// shared memory); then groups of G lanes stream the rows, each lane moving 16 bytes
+// of every neighbour row.  For k * sizeof(T) <= 16 one lane owns a whole row.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "mbl_device.cuh"
+#include "mbl_internal.h"
+
+namespace mbl {
+
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Vec {
+    T v[V];
+};
+
+template <typename T, int K>
+struct RowLayout {
+    static constexpr int kBytes = K * (int)sizeof(T);
+    static constexpr int V = kBytes >= 16 ? 16 / (int)sizeof(T) : K;  // elements per lane
+    static constexpr int G = K / V;                                    // lanes per row
+    static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
+};
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxNb = 32;  // at most |B| <= 32 neighbours per row
+
+// What the product kernel does with each finished output row.
+enum ApplyMode {
+    kPlain = 0,    // Y = (H - sigma) X
+    kPcgT = 1,     // t = (H - sigma) p; accumulate t.t per column; finish alpha = rz / t.t
+    kPcgQ = 2,     // q = (H - sigma) t; r -= alpha q; accumulate r.(dinv r); finish beta
+};
+
+// Per-column PCG scalars (FP64), laid out as arrays of kMaxK.
+struct PcgScalars {
+    double *rz, *rz0, *alpha, *beta;
+    int *active;
+    double tol2;  // pcg_tol^2 (0: never freeze)
+};
+
+struct Reduce {
+    double *partials;   // [gridDim.x][k]
+    unsigned *counter;  // zero on entry; the last block resets it
+};
+
+// ---------------------------------------------------------------------------------
+// Per-row index work: state, shifted diagonal and neighbour ranks.
+template <typename T>
+__device__ __forceinline__ int row_neighbours(const uint32_t *sb, const ChainParams &cp, uint32_t r,
+                                              uint32_t s, uint32_t *nb)
+{
+    int f = 0;
+    uint32_t fm = (s ^ (s >> 1)) & cp.open_mask;
+    while (fm) {
+        int i = __ffs(fm) - 1;
+        fm &= fm - 1;
+        int c = __popc(s & ((1u << i) - 1u));
+        uint32_t d = binom(sb, i, c);
+        nb[f++] = ((s >> i) & 1u) ? r + d : r - d;
+    }
+    if (cp.periodic && (((s >> (cp.L - 1)) ^ s) & 1u)) {
+        nb[f++] = cns_rank(sb, s ^ (1u | (1u << (cp.L - 1))));
+    }
+    return f;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ Vec<T, V> ldv(const T *p)
+{
+    return *reinterpret_cast<const Vec<T, V> *>(p);
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stv(T *p, const Vec<T, V> &x)
+{
+    *reinterpret_cast<Vec<T, V> *>(p) = x;
+}
+
+// Gather the neighbour rows listed in nbl[0..f) into acc: chunks of 8 independent
+// 16-byte loads are issued before any of them is consumed.
+template <typename T, int V>
+__device__ __forceinline__ void gather_add(T (&acc)[V], const T *__restrict__ X, int64_t ldx, int col, int f,
+                                           const uint32_t *nbl)
+{
+    const T half = (T)0.5;
+    for (int u = 0; u < f; u += 8) {
+        Vec<T, V> a[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) a[j].v[v] = (T)0;
+            if (u + j < f) a[j] = ldv<T, V>(X + (int64_t)nbl[u + j] * ldx + col);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += half * a[j].v[v];
+    }
+}
+
+// Two rows at once (16 loads in flight per lane).
+template <typename T, int V>
+__device__ __forceinline__ void gather_add2(T (&acc0)[V], T (&acc1)[V], const T *__restrict__ X, int64_t ldx, int col,
+                                            int f0, const uint32_t *nb0, int f1, const uint32_t *nb1)
+{
+    const T half = (T)0.5;
+    const int fm = f0 > f1 ? f0 : f1;
+    for (int u = 0; u < fm; u += 8) {
+        Vec<T, V> a[8], b[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                a[j].v[v] = (T)0;
+                b[j].v[v] = (T)0;
+            }
+            if (u + j < f0) a[j] = ldv<T, V>(X + (int64_t)nb0[u + j] * ldx + col);
+            if (u + j < f1) b[j] = ldv<T, V>(X + (int64_t)nb1[u + j] * ldx + col);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                acc0[v] += half * a[j].v[v];
+                acc1[v] += half * b[j].v[v];
+            }
+    }
+}
+
+// Epilogue of one output row: store (and accumulate t.t), or fold into the PCG
+// residual update r -= alpha q (and accumulate r.(M^-1 r)).
+template <typename T, int V, int MODE>
+__device__ __forceinline__ void finish_row(const T (&acc)[V], int f, uint32_t r, T *__restrict__ Y, int64_t ldy,
+                                           T *__restrict__ R, const T *__restrict__ dinv, int col, const T (&alpha)[V],
+                                           T (&part)[V])
+{
+    if (f < 0) return;
+    if (MODE == 0 || MODE == 1) {
+        Vec<T, V> y;
+#pragma unroll
+        for (int v = 0; v < V; ++v) y.v[v] = acc[v];
+        stv<T, V>(Y + (int64_t)r * ldy + col, y);
+        if (MODE == 1) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) part[v] += acc[v] * acc[v];
+        }
+    } else {
+        Vec<T, V> rr = ldv<T, V>(R + (int64_t)r * ldy + col);
+        const T di = dinv[r];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            rr.v[v] -= alpha[v] * acc[v];
+            part[v] += rr.v[v] * (di * rr.v[v]);
+        }
+        stv<T, V>(R + (int64_t)r * ldy + col, rr);
+    }
+}
+
+// Shared-memory scratch of one product block.
+template <typename T>
+struct ApplySmem {
+    uint32_t binom[kBinomDim * kBinomDim];
+    T tab[1024];
+    uint32_t nb[kWarps][32][kMaxNb + 1];  // neighbour lists, stride 33 words
+    T dsig[kWarps][32];
+    int cnt[kWarps][32];
+    T red[kWarps][64];
+};
+
+// Reduce per-lane column partials (lanes with equal lane % G share columns) over the
+// block, write this block's k partials, and let the last block finish.  Returns true
+// in the last block (after a __syncthreads, with the block's partial visible).
+template <typename T, int V, int G>
+__device__ __forceinline__ bool block_column_reduce(ApplySmem<T> &sm, T (&part)[V], int k,
+                                                    const Reduce &rd)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        for (int off = G; off < 32; off <<= 1) part[v] += __shfl_xor_sync(0xffffffffu, part[v], off);
+    if (lane < G) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) sm.red[warp][lane * V + v] = part[v];
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double acc = 0.0;
+        for (int w = 0; w < kWarps; ++w) acc += (double)sm.red[w][threadIdx.x];
+        rd.partials[(int64_t)blockIdx.x * k + threadIdx.x] = acc;
+    }
+    __threadfence();
+    __shared__ unsigned s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ticket = atomicAdd(rd.counter, 1u);
+        s_last = (ticket == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    return true;
+}
+
+// In the last block: total[c] = sum over blocks (fixed order) of partials, using
+// kThreads / k threads per column and a fixed-shape tree.
+__device__ __forceinline__ void finish_column_sums(const Reduce &rd, int k, double *total)
+{
+    __shared__ double s_tree[kThreads];
+    const int per = kThreads / k;  // threads per column (k divides 256 or per >= 1)
+    const int c = threadIdx.x / per, j = threadIdx.x % per;
+    double acc = 0.0;
+    if (c < k) {
+        for (int b = j; b < (int)gridDim.x; b += per) acc += rd.partials[(int64_t)b * k + c];
+    }
+    s_tree[threadIdx.x] = acc;
+    __syncthreads();
+    if (c < k && j == 0) {
+        double t = 0.0;
+        for (int q = 0; q < per; ++q) t += s_tree[threadIdx.x + q];
+        total[c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *rd.counter = 0u;
+}
+
+// ---------------------------------------------------------------------------------
+// The product kernel.  K = compile-time block width (row-major rows of K elements at
+// stride ldx / ldy).  Grid-stride loop over batches of 32 consecutive rows per warp.
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(kThreads) k_apply(ChainParams cp, const T *__restrict__ X, int64_t ldx,
+                                                    T *__restrict__ Y, int64_t ldy, uint32_t n,
+                                                    T *__restrict__ R, const T *__restrict__ dinv,
+                                                    PcgScalars ps, Reduce rd)
+{
+    using Lay = RowLayout<T, K>;
+    constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ApplySmem<T> &sm = *reinterpret_cast<ApplySmem<T> *>(smem_raw);
+    load_binom(sm.binom);
+    build_field_tables<T>(sm.tab, cp);
+    __syncthreads();
+
+    const T dconst = (T)cp.diag_const, hdelta = (T)cp.half_delta;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = (lane % G) * V;
+    T part[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) part[v] = (T)0;
+    T alpha[V];
+    if (MODE == kPcgQ) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) alpha[v] = (T)ps.alpha[col + v];
+    }
+
+    const uint32_t nbatch = (n + 31u) / 32u;
+    for (uint32_t b = blockIdx.x * kWarps + warp; b < nbatch; b += gridDim.x * kWarps) {
+        const uint32_t base = b * 32u;
+        if constexpr (G == 1) {
+            const uint32_t r = base + lane;
+            if (r < n) {
+                uint32_t s = state_of(sm.binom, cp, r);
+                T d = diag_shifted<T>(sm.tab, dconst, hdelta, cp, s);
+                uint32_t *nbl = sm.nb[warp][lane];
+                int f = row_neighbours<T>(sm.binom, cp, r, s, nbl);
+                Vec<T, V> x = ldv<T, V>(X + (int64_t)r * ldx);
+                T acc[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = d * x.v[v];
+                gather_add<T, V>(acc, X, ldx, 0, f, nbl);
+                if (MODE == kPlain || MODE == kPcgT) {
+                    Vec<T, V> y;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) y.v[v] = acc[v];
+                    stv<T, V>(Y + (int64_t)r * ldy, y);
+                    if (MODE == kPcgT) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) part[v] += acc[v] * acc[v];
+                    }
+                } else {
+                    Vec<T, V> rr = ldv<T, V>(R + (int64_t)r * ldy);
+                    T di = dinv[r];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        rr.v[v] -= alpha[v] * acc[v];
+                        part[v] += rr.v[v] * (di * rr.v[v]);
+                    }
+                    stv<T, V>(R + (int64_t)r * ldy, rr);
+                }
+            }
+        } else {
+            // phase 1: lane t ranks row base + t
+            {
+                const uint32_t r = base + lane;
+                int f = 0;
+                T d = (T)0;
+                if (r < n) {
+                    uint32_t s = state_of(sm.binom, cp, r);
+                    d = diag_shifted<T>(sm.tab, dconst, hdelta, cp, s);
+                    f = row_neighbours<T>(sm.binom, cp, r, s, sm.nb[warp][lane]);
+                }
+                sm.dsig[warp][lane] = d;
+                sm.cnt[warp][lane] = (r < n) ? f : -1;
+            }
+            __syncwarp();
+            // phase 2: groups of G lanes stream the rows, two rows per group at a time
+#pragma unroll 1
+            for (int sub = 0; sub < G; sub += 2) {
+                const int ri0 = sub * RPW + lane / G;
+                const int ri1 = ri0 + RPW;  // sub + 1 < G because G is even here
+                const int f0 = sm.cnt[warp][ri0], f1 = sm.cnt[warp][ri1];
+                const uint32_t r0 = base + ri0, r1 = base + ri1;
+                T acc0[V], acc1[V];
+                {
+                    Vec<T, V> x0, x1;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        x0.v[v] = (T)0;
+                        x1.v[v] = (T)0;
+                    }
+                    if (f0 >= 0) x0 = ldv<T, V>(X + (int64_t)r0 * ldx + col);
+                    if (f1 >= 0) x1 = ldv<T, V>(X + (int64_t)r1 * ldx + col);
+                    const T d0 = sm.dsig[warp][ri0], d1 = sm.dsig[warp][ri1];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        acc0[v] = d0 * x0.v[v];
+                        acc1[v] = d1 * x1.v[v];
+                    }
+                }
+                gather_add2<T, V>(acc0, acc1, X, ldx, col, f0, sm.nb[warp][ri0], f1, sm.nb[warp][ri1]);
+                finish_row<T, V, MODE>(acc0, f0, r0, Y, ldy, R, dinv, col, alpha, part);
+                finish_row<T, V, MODE>(acc1, f1, r1, Y, ldy, R, dinv, col, alpha, part);
+            }
+            __syncwarp();
+        }
+    }
+
+    if (MODE == kPlain) return;
+    if (!block_column_reduce<T, V, G>(sm, part, K, rd)) return;
+    __shared__ double s_tot[64];
+    finish_column_sums(rd, K, s_tot);
+    if (threadIdx.x < K) {
+        const int c = threadIdx.x;
+        if (MODE == kPcgT) {
+            double tt = s_tot[c];
+            bool ok = ps.active[c] && tt > 0.0 && isfinite(tt);
+            ps.alpha[c] = ok ? ps.rz[c] / tt : 0.0;
+        } else {
+            double rzn = s_tot[c];
+            int act = ps.active[c];
+            if (!isfinite(rzn)) act = 0;
+            if (ps.tol2 > 0.0 && rzn <= ps.tol2 * ps.rz0[c]) act = 0;
+            ps.beta[c] = (act && ps.rz[c] > 0.0) ? rzn / ps.rz[c] : 0.0;
+            if (!act) ps.alpha[c] = 0.0;
+            ps.active[c] = act;
+            ps.rz[c] = rzn;
+        }
+    }
+}
+
+// Runtime block width (any 1 <= k <= 256, any alignment): one warp per row, lanes
+// stride the columns.  Plain product only.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_apply_generic(ChainParams cp, const T *__restrict__ X,
+                                                            int64_t ldx, T *__restrict__ Y, int64_t ldy,
+                                                            uint32_t n, int k)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ApplySmem<T> &sm = *reinterpret_cast<ApplySmem<T> *>(smem_raw);
+    load_binom(sm.binom);
+    build_field_tables<T>(sm.tab, cp);
+    __syncthreads();
+    const T dconst = (T)cp.diag_const, hdelta = (T)cp.half_delta, half = (T)0.5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nbatch = (n + 31u) / 32u;
+    for (uint32_t b = blockIdx.x * kWarps + warp; b < nbatch; b += gridDim.x * kWarps) {
+        const uint32_t base = b * 32u;
+        {
+            const uint32_t r = base + lane;
+            int f = -1;
+            T d = (T)0;
+            if (r < n) {
+                uint32_t s = state_of(sm.binom, cp, r);
+                d = diag_shifted<T>(sm.tab, dconst, hdelta, cp, s);
+                f = row_neighbours<T>(sm.binom, cp, r, s, sm.nb[warp][lane]);
+            }
+            sm.dsig[warp][lane] = d;
+            sm.cnt[warp][lane] = f;
+        }
+        __syncwarp();
+        for (int ri = 0; ri < 32; ++ri) {
+            const int f = sm.cnt[warp][ri];
+            if (f < 0) break;
+            const uint32_t r = base + ri;
+            const T d = sm.dsig[warp][ri];
+            for (int c = lane; c < k; c += 32) {
+                T acc = d * X[(int64_t)r * ldx + c];
+                for (int u = 0; u < f; ++u) acc += half * X[(int64_t)sm.nb[warp][ri][u] * ldx + c];
+                Y[(int64_t)r * ldy + c] = acc;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Elementwise PCG kernels.
+
+// dinv[r] = 1 / ((d(s) - sigma)^2 + f(s)/4): inverse diagonal of A = (H - sigma)^2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fold_dinv(ChainParams cp, uint32_t n, T *__restrict__ dinv)
+{
+    __shared__ uint32_t sb[kBinomDim * kBinomDim];
+    __shared__ double tab[1024];
+    load_binom(sb);
+    build_field_tables<double>(tab, cp);
+    __syncthreads();
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        uint32_t s = state_of(sb, cp, r);
+        double d = diag_shifted<double>(tab, cp.diag_const, cp.half_delta, cp, s);
+        int f = __popc((s ^ (s >> 1)) & cp.open_mask);
+        if (cp.periodic) f += (int)(((s >> (cp.L - 1)) ^ s) & 1u);
+        dinv[r] = (T)(1.0 / (d * d + 0.25 * (double)f));
+    }
+}
+
+// Gershgorin bound max_s |d(s)| + f(s)/2 of ||H||: per-block maxima, last block folds.
+__global__ void __launch_bounds__(kThreads) k_gershgorin(ChainParams cp, uint32_t n, Reduce rd, double *out)
+{
+    __shared__ uint32_t sb[kBinomDim * kBinomDim];
+    __shared__ double tab[1024];
+    __shared__ double s_red[kThreads];
+    __shared__ unsigned s_last;
+    load_binom(sb);
+    build_field_tables<double>(tab, cp);
+    __syncthreads();
+    double m = 0.0;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        uint32_t s = state_of(sb, cp, r);
+        double d = diag_shifted<double>(tab, cp.diag_const, cp.half_delta, cp, s);  // sigma = 0 here
+        int f = __popc((s ^ (s >> 1)) & cp.open_mask);
+        if (cp.periodic) f += (int)(((s >> (cp.L - 1)) ^ s) & 1u);
+        m = fmax(m, fabs(d) + 0.5 * (double)f);
+    }
+    s_red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_red[threadIdx.x] = fmax(s_red[threadIdx.x], s_red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) rd.partials[blockIdx.x] = s_red[0];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(rd.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double g = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) g = fmax(g, rd.partials[b]);
+        *out = g;
+        *rd.counter = 0u;
+    }
+}
+
+// PCG start: r = b_j / ||b_j|| (b = FP64 residual block, norms given), p = dinv r,
+// w = 0; finish rz = r.(dinv r), rz0 = rz, active = rz > 0.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pcg_init(const double *__restrict__ B, int64_t ldb,
+                                                       const double *__restrict__ bnorm, uint32_t n, int k,
+                                                       const T *__restrict__ dinv, T *__restrict__ r,
+                                                       T *__restrict__ p, T *__restrict__ w, PcgScalars ps,
+                                                       Reduce rd)
+{
+    // thread layout: column c = threadIdx.x % k (k divides 256 when k is a power of two;
+    // otherwise threads with c >= ... still map columns in a round-robin way)
+    __shared__ double s_part[kThreads];
+    __shared__ unsigned s_last;
+    const int per = kThreads / k;  // rows per block-iteration
+    const int c = threadIdx.x % k, ro = threadIdx.x / k;
+    double acc = 0.0;
+    if (ro < per) {
+        const double inv = bnorm[c] > 0.0 ? 1.0 / bnorm[c] : 0.0;
+        for (uint32_t row = blockIdx.x * per + ro; row < n; row += gridDim.x * per) {
+            T rv = (T)(B[(int64_t)row * ldb + c] * inv);
+            T zv = dinv[row] * rv;
+            r[(int64_t)row * k + c] = rv;
+            p[(int64_t)row * k + c] = zv;
+            w[(int64_t)row * k + c] = (T)0;
+            acc += (double)(rv * zv);
+        }
+    }
+    s_part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int q = 0; q < per; ++q) t += s_part[q * k + threadIdx.x];
+        rd.partials[(int64_t)blockIdx.x * k + threadIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(rd.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    __shared__ double s_tot[64];
+    finish_column_sums(rd, k, s_tot);
+    if (threadIdx.x < k) {
+        double rz = s_tot[threadIdx.x];
+        ps.rz[threadIdx.x] = rz;
+        ps.rz0[threadIdx.x] = rz;
+        ps.alpha[threadIdx.x] = 0.0;
+        ps.beta[threadIdx.x] = 0.0;
+        ps.active[threadIdx.x] = (rz > 0.0 && isfinite(rz)) ? 1 : 0;
+    }
+}
+
+// PCG direction update: w += alpha p_old; p = dinv r + beta p_old (per column scalars).
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) k_pcg_update(uint32_t n, const T *__restrict__ dinv,
+                                                         const T *__restrict__ r, T *__restrict__ p,
+                                                         T *__restrict__ w, PcgScalars ps)
+{
+    using Lay = RowLayout<T, K>;
+    constexpr int V = Lay::V, G = Lay::G;
+    const int col = (threadIdx.x % G) * V;
+    T a[V], bt[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        a[v] = (T)ps.alpha[col + v];
+        bt[v] = (T)ps.beta[col + v];
+    }
+    const uint32_t rows_per_block = kThreads / G;
+    for (uint32_t row = blockIdx.x * rows_per_block + threadIdx.x / G; row < n;
+         row += gridDim.x * rows_per_block) {
+        const int64_t o = (int64_t)row * K + col;
+        Vec<T, V> rv = ldv<T, V>(r + o), pv = ldv<T, V>(p + o), wv = ldv<T, V>(w + o);
+        const T di = dinv[row];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            wv.v[v] += a[v] * pv.v[v];
+            pv.v[v] = di * rv.v[v] + bt[v] * pv.v[v];
+        }
+        stv<T, V>(w + o, wv);
+        stv<T, V>(p + o, pv);
+    }
+}
+
+// Generic-k version of the PCG product kernels (one warp per row, lanes stride the
+// columns, k <= 64).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_apply_pcg_generic(ChainParams cp, const T *__restrict__ X,
+                                                                T *__restrict__ Y, uint32_t n, int k,
+                                                                T *__restrict__ R, const T *__restrict__ dinv,
+                                                                PcgScalars ps, Reduce rd)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ApplySmem<T> &sm = *reinterpret_cast<ApplySmem<T> *>(smem_raw);
+    load_binom(sm.binom);
+    build_field_tables<T>(sm.tab, cp);
+    __syncthreads();
+    const T dconst = (T)cp.diag_const, hdelta = (T)cp.half_delta, half = (T)0.5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T part[2] = {(T)0, (T)0};
+    const uint32_t nbatch = (n + 31u) / 32u;
+    for (uint32_t b = blockIdx.x * kWarps + warp; b < nbatch; b += gridDim.x * kWarps) {
+        const uint32_t base = b * 32u;
+        {
+            const uint32_t r = base + lane;
+            int f = -1;
+            T d = (T)0;
+            if (r < n) {
+                uint32_t s = state_of(sm.binom, cp, r);
+                d = diag_shifted<T>(sm.tab, dconst, hdelta, cp, s);
+                f = row_neighbours<T>(sm.binom, cp, r, s, sm.nb[warp][lane]);
+            }
+            sm.dsig[warp][lane] = d;
+            sm.cnt[warp][lane] = f;
+        }
+        __syncwarp();
+        for (int ri = 0; ri < 32; ++ri) {
+            const int f = sm.cnt[warp][ri];
+            if (f < 0) break;
+            const uint32_t r = base + ri;
+            const T d = sm.dsig[warp][ri];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                if (c >= k) break;
+                T acc = d * X[(int64_t)r * k + c];
+                for (int u = 0; u < f; ++u) acc += half * X[(int64_t)sm.nb[warp][ri][u] * k + c];
+                if (MODE == kPcgT) {
+                    Y[(int64_t)r * k + c] = acc;
+                    part[h] += acc * acc;
+                } else {
+                    T rv = R[(int64_t)r * k + c] - (T)ps.alpha[c] * acc;
+                    R[(int64_t)r * k + c] = rv;
+                    part[h] += rv * (dinv[r] * rv);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // block reduction: columns c = lane + 32h
+    if (lane < 32) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) sm.red[warp][lane + 32 * h] = part[h];
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double acc = 0.0;
+        for (int w = 0; w < kWarps; ++w) acc += (double)sm.red[w][threadIdx.x];
+        rd.partials[(int64_t)blockIdx.x * k + threadIdx.x] = acc;
+    }
+    __threadfence();
+    __shared__ unsigned s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(rd.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    __shared__ double s_tot[64];
+    finish_column_sums(rd, k, s_tot);
+    if (threadIdx.x < k) {
+        const int c = threadIdx.x;
+        if (MODE == kPcgT) {
+            double tt = s_tot[c];
+            bool ok = ps.active[c] && tt > 0.0 && isfinite(tt);
+            ps.alpha[c] = ok ? ps.rz[c] / tt : 0.0;
+        } else {
+            double rzn = s_tot[c];
+            int act = ps.active[c];
+            if (!isfinite(rzn)) act = 0;
+            if (ps.tol2 > 0.0 && rzn <= ps.tol2 * ps.rz0[c]) act = 0;
+            ps.beta[c] = (act && ps.rz[c] > 0.0) ? rzn / ps.rz[c] : 0.0;
+            if (!act) ps.alpha[c] = 0.0;
+            ps.active[c] = act;
+            ps.rz[c] = rzn;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pcg_update_generic(uint32_t n, int k, const T *__restrict__ dinv,
+                                                                 const T *__restrict__ r, T *__restrict__ p,
+                                                                 T *__restrict__ w, PcgScalars ps)
+{
+    const int64_t total = (int64_t)n * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % k);
+        const uint32_t row = (uint32_t)(e / k);
+        T pv = p[e];
+        w[e] += (T)ps.alpha[c] * pv;
+        p[e] = dinv[row] * r[e] + (T)ps.beta[c] * pv;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Host-side dispatch.
+
+static int g_num_sms = 0;
+
+int num_sms()
+{
+    if (g_num_sms == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        g_num_sms = v;
+    }
+    return g_num_sms;
+}
+
+int make_chain_params(const mbl_chain *chain, double sigma, ChainParams *cp)
+{
+    if (!chain || !chain->h_host) return MBL_ERR_ARG;
+    const int L = chain->L;
+    if (L < 2 || L > kMaxL || chain->n_up < 0 || chain->n_up > L) return MBL_ERR_ARG;
+    if (!std::isfinite(chain->delta) || !std::isfinite(sigma)) return MBL_ERR_ARG;
+    ChainParams p{};
+    p.L = L;
+    p.n_up = chain->n_up;
+    p.periodic = (chain->periodic && L > 2) ? 1 : 0;
+    p.nbonds = (L - 1) + p.periodic;
+    p.open_mask = (L - 1 >= 32) ? 0xffffffffu : ((1u << (L - 1)) - 1u);
+    double hsum = 0.0;
+    for (int i = 0; i < L; ++i) {
+        double hi = chain->h_host[i];
+        if (!std::isfinite(hi)) return MBL_ERR_ARG;
+        p.h[i] = hi;
+        hsum += hi;
+    }
+    p.half_delta = 0.5 * chain->delta;
+    p.diag_const = 0.25 * chain->delta * (double)p.nbonds - 0.5 * hsum - sigma;
+    *cp = p;
+    return MBL_OK;
+}
+
+template <typename T>
+static size_t apply_smem_bytes()
+{
+    return sizeof(ApplySmem<T>);
+}
+
+template <typename T, int K, int MODE>
+static cudaError_t launch_apply_k(const ChainParams &cp, const T *X, int64_t ldx, T *Y, int64_t ldy, uint32_t n,
+                                  T *R, const T *dinv, const PcgScalars &ps, const Reduce &rd, int grid,
+                                  cudaStream_t st)
+{
+    auto kern = k_apply<T, K, MODE>;
+    const size_t sm = apply_smem_bytes<T>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr_set = true;
+    }
+    kern<<<grid, kThreads, sm, st>>>(cp, X, ldx, Y, ldy, n, R, dinv, ps, rd);
+    return cudaGetLastError();
+}
+
+static int apply_grid(uint32_t n, int cap_per_sm)
+{
+    int64_t need = ((int64_t)n + 32 * kWarps - 1) / (32 * kWarps);
+    int64_t cap = (int64_t)num_sms() * cap_per_sm;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+template <typename T>
+static bool vec_ok(const void *p, int64_t ld, int K)
+{
+    const int bytes = K * (int)sizeof(T);
+    const int align = bytes >= 16 ? 16 : bytes;
+    return ((uintptr_t)p % align == 0) && ((ld * (int64_t)sizeof(T)) % align == 0);
+}
+
+template <typename T>
+static int dispatch_plain(const ChainParams &cp, const T *X, int64_t ldx, T *Y, int64_t ldy, uint32_t n, int k,
+                          cudaStream_t st)
+{
+    PcgScalars ps{};
+    Reduce rd{};
+    const int grid = apply_grid(n, 8);
+    cudaError_t e = cudaSuccess;
+    bool done = true;
+    if (vec_ok<T>(X, ldx, k) && vec_ok<T>(Y, ldy, k)) {
+        switch (k) {
+        case 1: e = launch_apply_k<T, 1, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
+        case 2: e = launch_apply_k<T, 2, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
+        case 4: e = launch_apply_k<T, 4, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
+        case 8: e = launch_apply_k<T, 8, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
+        case 16: e = launch_apply_k<T, 16, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
+        case 32: e = launch_apply_k<T, 32, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
+        case 64: e = launch_apply_k<T, 64, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
+        default: done = false;
+        }
+    } else {
+        done = false;
+    }
+    if (!done) {
+        const size_t sm = apply_smem_bytes<T>();
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_apply_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            attr_set = true;
+        }
+        k_apply_generic<T><<<grid, kThreads, sm, st>>>(cp, X, ldx, Y, ldy, n, k);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+int apply_device(const ChainParams &cp, int dtype, const void *X, int64_t ldx, void *Y, int64_t ldy, uint32_t n,
+                 int k, cudaStream_t st)
+{
+    if (dtype == MBL_F32)
+        return dispatch_plain<float>(cp, (const float *)X, ldx, (float *)Y, ldy, n, k, st);
+    return dispatch_plain<double>(cp, (const double *)X, ldx, (double *)Y, ldy, n, k, st);
+}
+
+template <typename T>
+int pcg_fold_dinv(const ChainParams &cp, uint32_t n, T *dinv, cudaStream_t st)
+{
+    int grid = (int)(((int64_t)n + kThreads - 1) / kThreads);
+    if (grid > num_sms() * 8) grid = num_sms() * 8;
+    k_fold_dinv<T><<<grid, kThreads, 0, st>>>(cp, n, dinv);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+template int pcg_fold_dinv<float>(const ChainParams &, uint32_t, float *, cudaStream_t);
+template int pcg_fold_dinv<double>(const ChainParams &, uint32_t, double *, cudaStream_t);
+
+int gershgorin_bound(const ChainParams &cp, uint32_t n, double *partials, unsigned *counter, double *out,
+                     cudaStream_t st)
+{
+    int grid = (int)(((int64_t)n + kThreads - 1) / kThreads);
+    if (grid > num_sms() * 4) grid = num_sms() * 4;
+    Reduce rd{partials, counter};
+    k_gershgorin<<<grid, kThreads, 0, st>>>(cp, n, rd, out);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+int pcg_grid(uint32_t n) { return apply_grid(n, 4); }
+
+template <typename T>
+int pcg_start(const double *B, int64_t ldb, const double *bnorm, uint32_t n, int k, const T *dinv, T *r, T *p,
+              T *w, const PcgDev &pd, cudaStream_t st)
+{
+    PcgScalars ps{pd.rz, pd.rz0, pd.alpha, pd.beta, pd.active, pd.tol2};
+    Reduce rd{pd.partials, pd.counter};
+    int grid = pcg_grid(n);
+    k_pcg_init<T><<<grid, kThreads, 0, st>>>(B, ldb, bnorm, n, k, dinv, r, p, w, ps, rd);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+template int pcg_start<float>(const double *, int64_t, const double *, uint32_t, int, const float *, float *,
+                              float *, float *, const PcgDev &, cudaStream_t);
+template int pcg_start<double>(const double *, int64_t, const double *, uint32_t, int, const double *, double *,
+                               double *, double *, const PcgDev &, cudaStream_t);
+
+template <typename T, int K>
+static cudaError_t pcg_step_k(const ChainParams &cp, uint32_t n, const T *dinv, T *r, T *p, T *t, T *w,
+                              const PcgScalars &ps, const Reduce &rd, int grid, cudaStream_t st)
+{
+    cudaError_t e = launch_apply_k<T, K, kPcgT>(cp, p, K, t, K, n, nullptr, dinv, ps, rd, grid, st);
+    if (e != cudaSuccess) return e;
+    e = launch_apply_k<T, K, kPcgQ>(cp, t, K, nullptr, K, n, r, dinv, ps, rd, grid, st);
+    if (e != cudaSuccess) return e;
+    int ugrid = (int)(((int64_t)n * RowLayout<T, K>::G + kThreads - 1) / kThreads);
+    if (ugrid > num_sms() * 8) ugrid = num_sms() * 8;
+    k_pcg_update<T, K><<<ugrid, kThreads, 0, st>>>(n, dinv, r, p, w, ps);
+    return cudaGetLastError();
+}
+
+// One PCG iteration on A = (H - sigma)^2: t = (H - sigma)p, alpha; r -= alpha (H - sigma)t,
+// beta; w += alpha p, p = M^-1 r + beta p.  Three launches, no host synchronisation.
+template <typename T>
+int pcg_step(const ChainParams &cp, uint32_t n, int k, const T *dinv, T *r, T *p, T *t, T *w, const PcgDev &pd,
+             cudaStream_t st)
+{
+    PcgScalars ps{pd.rz, pd.rz0, pd.alpha, pd.beta, pd.active, pd.tol2};
+    Reduce rd{pd.partials, pd.counter};
+    const int grid = pcg_grid(n);
+    cudaError_t e = cudaSuccess;
+    switch (k) {
+    case 8: e = pcg_step_k<T, 8>(cp, n, dinv, r, p, t, w, ps, rd, grid, st); break;
+    case 16: e = pcg_step_k<T, 16>(cp, n, dinv, r, p, t, w, ps, rd, grid, st); break;
+    case 32: e = pcg_step_k<T, 32>(cp, n, dinv, r, p, t, w, ps, rd, grid, st); break;
+    case 64: e = pcg_step_k<T, 64>(cp, n, dinv, r, p, t, w, ps, rd, grid, st); break;
+    default: {
+        const size_t sm = apply_smem_bytes<T>();
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_apply_pcg_generic<T, kPcgT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k_apply_pcg_generic<T, kPcgQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            attr_set = true;
+        }
+        k_apply_pcg_generic<T, kPcgT><<<grid, kThreads, sm, st>>>(cp, p, t, n, k, nullptr, dinv, ps, rd);
+        k_apply_pcg_generic<T, kPcgQ><<<grid, kThreads, sm, st>>>(cp, t, nullptr, n, k, r, dinv, ps, rd);
+        int ugrid = num_sms() * 8;
+        k_pcg_update_generic<T><<<ugrid, kThreads, 0, st>>>(n, k, dinv, r, p, w, ps);
+        e = cudaGetLastError();
+    }
+    }
+    return e == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+template int pcg_step<float>(const ChainParams &, uint32_t, int, const float *, float *, float *, float *, float *,
+                             const PcgDev &, cudaStream_t);
+template int pcg_step<double>(const ChainParams &, uint32_t, int, const double *, double *, double *, double *,
+                              double *, const PcgDev &, cudaStream_t);
+
+}  // namespace mbl
+
+// ---------------------------------------------------------------------------------
+// C ABI: the product.
+
+extern "C" int mbl_hamiltonian_apply(const mbl_chain *chain, double sigma, int dtype, const void *X_dev,
+                                     int64_t ldx, void *Y_dev, int64_t ldy, int64_t n, int k, mbl_stream_t stream)
+{
+    using namespace mbl;
+    ChainParams cp;
+    int rc = make_chain_params(chain, sigma, &cp);
+    if (rc != MBL_OK) return rc;
+    if (dtype != MBL_F32 && dtype != MBL_F64) return MBL_ERR_ARG;
+    if (k < 1 || k > 256 || ldx < k || ldy < k) return MBL_ERR_ARG;
+    if (n != mbl_basis_size(chain->L, chain->n_up)) return MBL_ERR_ARG;
+    if (n == 0) return MBL_OK;
+    if (!X_dev || !Y_dev) return MBL_ERR_ARG;
+    const size_t es = dtype == MBL_F32 ? 4 : 8;
+    // X and Y must not overlap (the gather reads X rows that other groups write in Y)
+    const char *xb = (const char *)X_dev, *yb = (const char *)Y_dev;
+    const char *xe = xb + ((n - 1) * ldx + k) * (int64_t)es, *ye = yb + ((n - 1) * ldy + k) * (int64_t)es;
+    if (xb < ye && yb < xe) return MBL_ERR_ARG;
+    return apply_device(cp, dtype, X_dev, ldx, Y_dev, ldy, (uint32_t)n, k, (cudaStream_t)stream);
+}

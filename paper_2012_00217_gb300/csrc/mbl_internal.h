@@ -1,0 +1,40 @@
+// mbl_internal.h -- host-side interfaces between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "mbl.h"
+
+namespace mbl {
+
+struct ChainParams;
+
+// Device-resident per-column PCG state plus the block-partials scratch used by the
+// deterministic reductions (partials: >= grid * 64 doubles; counter: one zeroed word).
+struct PcgDev {
+    double *rz, *rz0, *alpha, *beta;
+    int *active;
+    double tol2;
+    double *partials;
+    unsigned *counter;
+};
+
+int num_sms();
+int make_chain_params(const mbl_chain *chain, double sigma, ChainParams *cp);
+int apply_device(const ChainParams &cp, int dtype, const void *X, int64_t ldx, void *Y, int64_t ldy, uint32_t n,
+                 int k, cudaStream_t st);
+int gershgorin_bound(const ChainParams &cp, uint32_t n, double *partials, unsigned *counter, double *out,
+                     cudaStream_t st);
+int pcg_grid(uint32_t n);
+template <typename T>
+int pcg_fold_dinv(const ChainParams &cp, uint32_t n, T *dinv, cudaStream_t st);
+template <typename T>
+int pcg_start(const double *B, int64_t ldb, const double *bnorm, uint32_t n, int k, const T *dinv, T *r, T *p,
+              T *w, const PcgDev &pd, cudaStream_t st);
+template <typename T>
+int pcg_step(const ChainParams &cp, uint32_t n, int k, const T *dinv, T *r, T *p, T *t, T *w, const PcgDev &pd,
+             cudaStream_t st);
+
+}  // namespace mbl

@@ -1,0 +1,620 @@
+// mbl_lobpcg.cu -- folded-spectrum LOBPCG with a Jacobi-PCG preconditioner (Sec. 3.2,
+// Sec. 6.2), and the spectrum-bounds LOBPCG on +H / -H used to place sigma.
+//
+// One iteration (every product of H runs in the gather kernels of mbl_apply.cu; every
+// reduction is deterministic):
+//   1. H Rayleigh-Ritz on span(X): M = X^T (H - sigma)X, eig M = V mu V^T,
+//      E = (H - sigma)X - X M, residual_j = ||E v_j||; accept the nev values nearest 0.
+//   2. R = AX - X (X^T A X)              (A = (H - sigma)^2)
+//   3. W = PCG_m(R / ||R||) column-wise, Jacobi M = diag(A)      [FP32 in mixed mode]
+//   4. W <- W - X (X^T W), twice;  AW = A W
+//   5. P <- P - X (X^T P), twice;  AP = A P     (from the second iteration on)
+//   6. SVQB on S = [X W P] and Rayleigh-Ritz with A; keep the k smallest
+//   7. X <- S C_X, P <- [W P] C_[W,P] (unit columns), X <- Cholesky-QR(X)
+//   8. T = (H - sigma)X, AX = (H - sigma)T
+// Steps 2..8 plus step 1 of the next iteration are enqueued without host
+// synchronisation and can be captured once as a CUDA graph and replayed; the host
+// reads a few status words per iteration.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+
+#include "mbl_dense.h"
+#include "mbl_device.cuh"
+#include "mbl_internal.h"
+
+namespace mbl {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Carver {
+    size_t off = 0;
+    char *base = nullptr;
+    template <typename T>
+    T *take(size_t count)
+    {
+        size_t o = off;
+        off = align_up(off + count * sizeof(T));
+        return base ? reinterpret_cast<T *>(base + o) : nullptr;
+    }
+};
+
+// Device buffers of one solve (the workspace carve-up).
+struct Buffers {
+    double *S, *AS, *T, *Tmp, *Xn;
+    void *pr, *pp, *pt, *pw, *dinv;  // PCG vectors (float or double)
+    double *G1, *G2, *G3, *Gk;       // Grams: (3k)^2 x 2, k^2 x 2
+    double *part;                    // Gram / column partials
+    double *mu, *V, *Rinv, *coef, *theta, *Csel, *res_all, *res_sel, *rn, *eigw;
+    double *pcg_s;                   // rz, rz0, alpha, beta (4 x 64)
+    int *pcg_active;
+    double *pcg_part;
+    unsigned *counter;
+    int *iflags;                     // [0] chol flag, [1..2] rr info, [4..5] hrr status, [8..] sel
+    double *dstat;                   // [0] max rel resid, [1] gershgorin
+    uint32_t *states;                // sector basis, n words
+};
+
+// Largest scratch any reduction of the iteration needs: Grams of widths k, 2k, 3k and
+// the column norms.
+size_t part_doubles(int64_t n, int k)
+{
+    size_t m = colnorm_partial_doubles(k);
+    for (int w = 1; w <= 3; ++w) {
+        size_t a = gram_partial_doubles(n, w * k, w * k);
+        if (a > m) m = a;
+    }
+    return m;
+}
+
+Buffers carve(char *base, int64_t n, int k, int pcg_f32, size_t *bytes)
+{
+    Carver c;
+    c.base = base;
+    Buffers b{};
+    const size_t nk = (size_t)n * k;
+    const size_t es = pcg_f32 ? 4 : 8;
+    b.S = c.take<double>(3 * nk);
+    b.AS = c.take<double>(3 * nk);
+    b.T = c.take<double>(nk);
+    b.Tmp = c.take<double>(nk);
+    b.Xn = c.take<double>(nk);
+    b.pr = c.take<char>(nk * es);
+    b.pp = c.take<char>(nk * es);
+    b.pt = c.take<char>(nk * es);
+    b.pw = c.take<char>(nk * es);
+    b.dinv = c.take<char>((size_t)n * es);
+    const size_t w2 = (size_t)9 * k * k;
+    b.G1 = c.take<double>(w2);
+    b.G2 = c.take<double>(w2);
+    b.G3 = c.take<double>(w2);
+    b.Gk = c.take<double>((size_t)k * k);
+    b.part = c.take<double>(part_doubles(n, k));
+    b.mu = c.take<double>(3 * k);
+    b.V = c.take<double>((size_t)k * k);
+    b.Rinv = c.take<double>((size_t)k * k);
+    b.coef = c.take<double>(w2);
+    b.theta = c.take<double>(3 * k);
+    b.Csel = c.take<double>((size_t)k * k);
+    b.res_all = c.take<double>(k);
+    b.res_sel = c.take<double>(k);
+    b.rn = c.take<double>(k);
+    size_t ew = small_rr_work_doubles(3 * k);
+    size_t ew2 = small_eig_work_doubles(3 * k);
+    b.eigw = c.take<double>(ew > ew2 ? ew : ew2);
+    b.pcg_s = c.take<double>(4 * 64);
+    b.pcg_active = c.take<int>(64);
+    b.pcg_part = c.take<double>((size_t)pcg_grid((uint32_t)n) * 64 + 64);
+    b.counter = c.take<unsigned>(4);
+    b.iflags = c.take<int>(16 + 64);
+    b.dstat = c.take<double>(8);
+    b.states = c.take<uint32_t>((size_t)n);
+    *bytes = c.off;
+    return b;
+}
+
+int check_opts(const mbl_chain *chain, const mbl_lobpcg_opts *o, int64_t *n_out)
+{
+    if (!chain || !o) return MBL_ERR_ARG;
+    int64_t n = mbl_basis_size(chain->L, chain->n_up);
+    if (n <= 0 || chain->L < 2) return MBL_ERR_ARG;
+    if (o->k < 1 || o->k > 64 || o->nev < 1 || o->nev > o->k) return MBL_ERR_ARG;
+    if ((int64_t)3 * o->k > n) return MBL_ERR_ARG;
+    if (o->max_iter < 0 || o->pcg_iters < 0) return MBL_ERR_ARG;
+    if (!(o->tol > 0.0) || !(o->pcg_tol >= 0.0)) return MBL_ERR_ARG;
+    if (o->mode != MBL_MODE_FP64 && o->mode != MBL_MODE_MIXED) return MBL_ERR_ARG;
+    *n_out = n;
+    return MBL_OK;
+}
+
+#define MBL_TRY(expr)                   \
+    do {                                \
+        int rc__ = (expr);              \
+        if (rc__ != MBL_OK) return rc__; \
+    } while (0)
+
+// The solver state for one call.
+struct Solver {
+    ChainParams cp;
+    int64_t n;
+    int k, nev, m;
+    int mixed;
+    int largest;  // bounds mode, -H: keep the largest Ritz values
+    int folded;   // 1: A = (H - sigma)^2 with PCG; 0: A = H - sigma, no preconditioner
+    double tol_abs, norm_h, pcg_tol;
+    Buffers b;
+    cudaStream_t st;
+    int64_t matvecs = 0;
+    // optional phase timing: events recorded at the phase boundaries of each iteration
+    bool timing = false;
+    cudaEvent_t ev[10] = {};
+    double tphase[10] = {};
+    void mark(int i)
+    {
+        if (timing) cudaEventRecord(ev[i], st);
+    }
+    void accumulate(int first, int last, int slot0)  // tphase[slot0 + j] += ev[first+j] -> ev[first+j+1]
+    {
+        if (!timing) return;
+        for (int i = first; i < last; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) tphase[slot0 + i - first] += 1e-3 * ms;
+        }
+    }
+
+    double *X() { return b.S; }
+    double *W() { return b.S + k; }
+    double *P() { return b.S + 2 * k; }
+    double *AX() { return b.AS; }
+    double *AW() { return b.AS + k; }
+    double *AP() { return b.AS + 2 * k; }
+    int64_t ld3() const { return 3 * (int64_t)k; }
+
+    int apply64(const double *Xp, int64_t ldx, double *Yp, int64_t ldy)
+    {
+        matvecs += k;
+        return apply_device(cp, MBL_F64, Xp, ldx, Yp, ldy, (uint32_t)n, k, st);
+    }
+    // Y = A X: two products through Tmp when folded
+    int applyA(const double *Xp, int64_t ldx, double *Yp, int64_t ldy)
+    {
+        if (!folded) return apply64(Xp, ldx, Yp, ldy);
+        MBL_TRY(apply64(Xp, ldx, b.Tmp, k));
+        return apply64(b.Tmp, k, Yp, ldy);
+    }
+    // X <- X - X_ref (X_ref^T X), twice (block classical Gram-Schmidt against X)
+    int ortho_against_x(double *Bp)
+    {
+        for (int pass = 0; pass < 2; ++pass) {
+            MBL_TRY(gram(X(), ld3(), k, Bp, ld3(), k, n, b.Gk, k, 0, 0, b.part, st));
+            MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, Bp, ld3(), Bp, ld3(), n, -1.0, 1.0, 0, st));
+        }
+        return MBL_OK;
+    }
+    // X <- Cholesky-QR(src) into the X slice; flag -> iflags[0]
+    int cholqr_into_x(const double *src, int64_t lds)
+    {
+        MBL_TRY(gram(src, lds, k, src, lds, k, n, b.Gk, k, 1, 0, b.part, st));
+        MBL_TRY(small_chol_inv(k, b.Gk, k, b.Rinv, b.eigw, b.iflags + 0, st));
+        return update(src, lds, k, b.Rinv, k, k, nullptr, 0, X(), ld3(), n, 1.0, 0.0, 0, st);
+    }
+    int refresh_tx()  // T = (H - sigma)X, AX = (H - sigma)T   (or AX = T when unfolded)
+    {
+        MBL_TRY(apply64(X(), ld3(), b.T, k));
+        if (folded) return apply64(b.T, k, AX(), ld3());
+        return copy_block(b.T, k, AX(), ld3(), k, n, st);
+    }
+    // Step 1: H Rayleigh-Ritz on span(X) and the convergence status (folded mode).
+    int enqueue_hrr()
+    {
+        MBL_TRY(gram(X(), ld3(), k, b.T, k, k, n, b.Gk, k, 1, 0, b.part, st));
+        MBL_TRY(small_eig(k, b.Gk, k, b.mu, b.V, b.eigw, st));
+        MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, b.T, k, b.Tmp, k, n, -1.0, 1.0, 0, st));
+        MBL_TRY(gram(b.Tmp, k, k, b.Tmp, k, k, n, b.G3, k, 1, mixed, b.part, st));
+        return hrr_select(k, nev, b.mu, b.V, b.G3, tol_abs, norm_h, b.res_all, b.iflags + 8, b.res_sel,
+                          b.iflags + 4, b.dstat, st);
+    }
+    // Bounds mode status: theta_0 and ||R_0|| from AX = H X (sign handled by 'largest').
+    int enqueue_bounds_status()
+    {
+        MBL_TRY(gram(X(), ld3(), k, AX(), ld3(), k, n, b.Gk, k, 1, 0, b.part, st));
+        MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, AX(), ld3(), b.Tmp, k, n, -1.0, 1.0, 0, st));
+        MBL_TRY(colnorms(b.Tmp, k, k, n, b.rn, 1, b.part, st));
+        return MBL_OK;
+    }
+    // Steps 2..8 (+ the status of the next iteration).
+    int enqueue_body(bool have_p)
+    {
+        // 2. residual of the current block
+        mark(0);
+        MBL_TRY(gram(X(), ld3(), k, AX(), ld3(), k, n, b.Gk, k, 1, mixed, b.part, st));
+        MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, AX(), ld3(), b.Tmp, k, n, -1.0, 1.0, 0, st));
+        mark(1);
+        if (folded) {
+            // 3. preconditioner
+            MBL_TRY(colnorms(b.Tmp, k, k, n, b.rn, 1, b.part, st));
+            PcgDev pd{b.pcg_s, b.pcg_s + 64, b.pcg_s + 128, b.pcg_s + 192, b.pcg_active, pcg_tol * pcg_tol,
+                      b.pcg_part, b.counter};
+            if (mixed) {
+                MBL_TRY(pcg_start<float>(b.Tmp, k, b.rn, (uint32_t)n, k, (const float *)b.dinv, (float *)b.pr,
+                                         (float *)b.pp, (float *)b.pw, pd, st));
+                for (int it = 0; it < m; ++it)
+                    MBL_TRY(pcg_step<float>(cp, (uint32_t)n, k, (const float *)b.dinv, (float *)b.pr, (float *)b.pp,
+                                            (float *)b.pt, (float *)b.pw, pd, st));
+            } else {
+                MBL_TRY(pcg_start<double>(b.Tmp, k, b.rn, (uint32_t)n, k, (const double *)b.dinv, (double *)b.pr,
+                                          (double *)b.pp, (double *)b.pw, pd, st));
+                for (int it = 0; it < m; ++it)
+                    MBL_TRY(pcg_step<double>(cp, (uint32_t)n, k, (const double *)b.dinv, (double *)b.pr,
+                                             (double *)b.pp, (double *)b.pt, (double *)b.pw, pd, st));
+            }
+            matvecs += (int64_t)2 * m * k;
+            MBL_TRY(widen(mixed, b.pw, k, W(), ld3(), k, n, st));
+        } else {
+            MBL_TRY(copy_block(b.Tmp, k, W(), ld3(), k, n, st));
+        }
+        mark(2);
+        // 4. W against X, then A W
+        MBL_TRY(ortho_against_x(W()));
+        MBL_TRY(applyA(W(), ld3(), AW(), ld3()));
+        // 5. P against X, then A P
+        if (have_p) {
+            MBL_TRY(ortho_against_x(P()));
+            MBL_TRY(applyA(P(), ld3(), AP(), ld3()));
+        }
+        mark(3);
+        // 6. SVQB + Rayleigh-Ritz with A
+        const int w = have_p ? 3 * k : 2 * k;
+        MBL_TRY(gram(b.S, ld3(), w, b.S, ld3(), w, n, b.G1, w, 1, mixed, b.part, st));
+        MBL_TRY(gram(b.S, ld3(), w, b.AS, ld3(), w, n, b.G2, w, 1, mixed, b.part, st));
+        mark(4);
+        MBL_TRY(small_svqb_rr(w, k, largest, mixed, b.G1, b.G2, svqb_tau(), b.coef, b.theta, b.eigw, b.iflags + 1, st));
+        mark(5);
+        // 7. updates
+        MBL_TRY(update(b.S, ld3(), w, b.coef, k, k, nullptr, 0, b.Xn, k, n, 1.0, 0.0, 0, st));
+        MBL_TRY(update(W(), ld3(), w - k, b.coef + (int64_t)k * k, k, k, nullptr, 0, P(), ld3(), n, 1.0, 0.0, 0, st));
+        MBL_TRY(colnorms(P(), ld3(), k, n, b.rn, 1, b.part, st));
+        MBL_TRY(scale_cols_inv(P(), ld3(), k, n, b.rn, st));
+        MBL_TRY(cholqr_into_x(b.Xn, k));
+        mark(6);
+        // 8. products for the new block, and the status of the next iteration
+        MBL_TRY(refresh_tx());
+        mark(7);
+        MBL_TRY(folded ? enqueue_hrr() : enqueue_bounds_status());
+        mark(8);
+        return MBL_OK;
+    }
+    // Directions below the resolution of the Gram matrix are dropped: its entries carry
+    // FP32 rounding in mixed mode.
+    double svqb_tau() const { return mixed ? 1e-7 : 1e-14; }
+};
+
+// The rotation of the start block onto A's Ritz vectors (X, T, AX <- . C).
+int initial_rr(Solver &s)
+{
+    MBL_TRY(gram(s.X(), s.ld3(), s.k, s.AX(), s.ld3(), s.k, s.n, s.b.Gk, s.k, 1, 0, s.b.part, s.st));
+    MBL_TRY(small_eig(s.k, s.b.Gk, s.k, s.b.mu, s.b.V, s.b.eigw, s.st));
+    if (s.largest) {
+        // reverse column order so that column 0 is the largest Ritz value
+        // (done by a tiny gather with reversed indices)
+        int sel_rev[64];
+        for (int j = 0; j < s.k; ++j) sel_rev[j] = s.k - 1 - j;
+        MBL_TRY(cudaMemcpyAsync(s.b.iflags + 8, sel_rev, sizeof(int) * s.k, cudaMemcpyHostToDevice, s.st) ==
+                        cudaSuccess
+                    ? MBL_OK
+                    : MBL_ERR_CUDA);
+        MBL_TRY(gather_cols(s.k, s.k, s.b.V, s.b.iflags + 8, s.b.Csel, s.st));
+        // keep the host array alive until the copy is done
+        if (cudaStreamSynchronize(s.st) != cudaSuccess) return MBL_ERR_CUDA;
+    } else {
+        MBL_TRY(copy_block(s.b.V, s.k, s.b.Csel, s.k, s.k, s.k, s.st));
+    }
+    MBL_TRY(update(s.X(), s.ld3(), s.k, s.b.Csel, s.k, s.k, nullptr, 0, s.b.Xn, s.k, s.n, 1.0, 0.0, 0, s.st));
+    MBL_TRY(copy_block(s.b.Xn, s.k, s.X(), s.ld3(), s.k, s.n, s.st));
+    return s.refresh_tx();
+}
+
+struct HostStatus {
+    int iflags[16];
+    double dstat[8];
+};
+
+int read_status(Solver &s, HostStatus *h)
+{
+    if (cudaMemcpyAsync(h->iflags, s.b.iflags, sizeof(h->iflags), cudaMemcpyDeviceToHost, s.st) != cudaSuccess)
+        return MBL_ERR_CUDA;
+    if (cudaMemcpyAsync(h->dstat, s.b.dstat, sizeof(h->dstat), cudaMemcpyDeviceToHost, s.st) != cudaSuccess)
+        return MBL_ERR_CUDA;
+    if (cudaStreamSynchronize(s.st) != cudaSuccess) return MBL_ERR_CUDA;
+    return MBL_OK;
+}
+
+// Capture body(have_p) once into an executable graph.
+struct GraphCache {
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;
+    ~GraphCache()
+    {
+        for (auto &e : exec)
+            if (e) cudaGraphExecDestroy(e);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+int run_body(Solver &s, bool have_p, bool use_graph, GraphCache &gc)
+{
+    if (!use_graph) return s.enqueue_body(have_p);
+    const int slot = have_p ? 1 : 0;
+    if (!gc.exec[slot]) {
+        if (!gc.cap && cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking) != cudaSuccess) return MBL_ERR_CUDA;
+        cudaStream_t user = s.st;
+        s.st = gc.cap;
+        int64_t mv = s.matvecs;
+        if (cudaStreamBeginCapture(gc.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            s.st = user;
+            return MBL_ERR_CUDA;
+        }
+        int rc = s.enqueue_body(have_p);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(gc.cap, &g);
+        s.st = user;
+        s.matvecs = mv;  // counted again at each replay below
+        if (rc != MBL_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess || !g) return MBL_ERR_CUDA;
+        ce = cudaGraphInstantiate(&gc.exec[slot], g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return MBL_ERR_CUDA;
+    }
+    // matvec accounting of one body
+    s.matvecs += (int64_t)(s.folded ? 2 * s.m * s.k + 2 * s.k + (have_p ? 2 * s.k : 0) + 2 * s.k
+                                    : s.k + (have_p ? s.k : 0) + s.k);
+    return cudaGraphLaunch(gc.exec[slot], s.st) == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+}  // namespace
+
+}  // namespace mbl
+
+using namespace mbl;
+
+extern "C" int mbl_lobpcg_workspace_size(const mbl_chain *chain, const mbl_lobpcg_opts *opts, size_t *bytes)
+{
+    int64_t n;
+    if (!bytes) return MBL_ERR_ARG;
+    int rc = check_opts(chain, opts, &n);
+    if (rc != MBL_OK) return rc;
+    carve(nullptr, n, opts->k, opts->mode == MBL_MODE_MIXED, bytes);
+    return MBL_OK;
+}
+
+extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
+                                const double *X0_dev, void *workspace_dev, size_t workspace_bytes,
+                                double *evals_host, double *evecs_dev, double *resid_host, mbl_lobpcg_stats *stats,
+                                mbl_stream_t stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    int64_t n;
+    int rc = check_opts(chain, opts, &n);
+    if (rc != MBL_OK) return rc;
+    if (!X0_dev || !workspace_dev) return MBL_ERR_ARG;
+    if ((uintptr_t)workspace_dev % kAlign) return MBL_ERR_ARG;
+    Solver s;
+    rc = make_chain_params(chain, sigma, &s.cp);
+    if (rc != MBL_OK) return rc;
+    size_t need = 0;
+    const int mixed = opts->mode == MBL_MODE_MIXED;
+    s.b = carve((char *)workspace_dev, n, opts->k, mixed, &need);
+    if (workspace_bytes < need) return MBL_ERR_WORKSPACE;
+    s.n = n;
+    s.k = opts->k;
+    s.nev = opts->nev;
+    s.m = opts->pcg_iters;
+    s.mixed = mixed;
+    s.largest = 0;
+    s.folded = 1;
+    s.pcg_tol = opts->pcg_tol;
+    s.st = (cudaStream_t)stream;
+    const int k = s.k;
+
+    if (cudaMemsetAsync(s.b.counter, 0, 4 * sizeof(unsigned), s.st) != cudaSuccess ||
+        cudaMemsetAsync(s.b.iflags, 0, (16 + 64) * sizeof(int), s.st) != cudaSuccess)
+        return MBL_ERR_CUDA;
+    s.timing = opts->timing != 0;
+    if (s.timing) {
+        for (auto &e : s.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return MBL_ERR_CUDA;
+        s.mark(9);
+    }
+    // sector basis, read by every product kernel of the solve
+    MBL_TRY(mbl_basis_build(chain->L, chain->n_up, s.b.states, n, stream));
+    s.cp.states = s.b.states;
+    // norm used to scale the tolerance
+    double norm_h = opts->norm_h;
+    if (!(norm_h > 0.0)) {
+        ChainParams c0;
+        make_chain_params(chain, 0.0, &c0);
+        MBL_TRY(gershgorin_bound(c0, (uint32_t)n, s.b.part, s.b.counter, s.b.dstat + 1, s.st));
+        if (cudaMemcpyAsync(&norm_h, s.b.dstat + 1, sizeof(double), cudaMemcpyDeviceToHost, s.st) != cudaSuccess ||
+            cudaStreamSynchronize(s.st) != cudaSuccess)
+            return MBL_ERR_CUDA;
+    }
+    s.norm_h = norm_h;
+    s.tol_abs = opts->tol * norm_h;
+
+    // Jacobi preconditioner diagonal
+    if (mixed)
+        MBL_TRY(pcg_fold_dinv<float>(s.cp, (uint32_t)n, (float *)s.b.dinv, s.st));
+    else
+        MBL_TRY(pcg_fold_dinv<double>(s.cp, (uint32_t)n, (double *)s.b.dinv, s.st));
+
+    // start block: orthonormalise, products, rotate onto A's Ritz vectors
+    MBL_TRY(s.cholqr_into_x(X0_dev, k));
+    MBL_TRY(s.refresh_tx());
+    MBL_TRY(initial_rr(s));
+    MBL_TRY(s.enqueue_hrr());
+    if (s.timing) cudaEventRecord(s.ev[0], s.st);
+
+    HostStatus hs;
+    GraphCache gc;
+    int it = 0;
+    bool have_p = false;
+    int status = MBL_OK;
+    const bool graphs = opts->use_graph != 0 && !s.timing;
+    for (;;) {
+        MBL_TRY(read_status(s, &hs));
+        if (s.timing) {
+            if (it == 0) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, s.ev[9], s.ev[0]) == cudaSuccess) s.tphase[9] += 1e-3 * ms;
+            } else {
+                s.accumulate(0, 8, 0);
+            }
+        }
+        if (hs.iflags[5] || hs.iflags[2]) {
+            status = MBL_ERR_NUMERIC;
+            break;
+        }
+        if (hs.iflags[0]) {
+            status = MBL_ERR_BREAKDOWN;
+            break;
+        }
+        if (hs.iflags[4]) break;
+        if (it >= opts->max_iter) {
+            status = MBL_ERR_NOT_CONVERGED;
+            break;
+        }
+        MBL_TRY(run_body(s, have_p, graphs, gc));
+        have_p = true;
+        ++it;
+    }
+    // final extraction: evecs = X V[:, sel]
+    MBL_TRY(gather_cols(k, s.nev, s.b.V, s.b.iflags + 8, s.b.Csel, s.st));
+    if (evecs_dev)
+        MBL_TRY(update(s.X(), s.ld3(), k, s.b.Csel, s.nev, s.nev, nullptr, 0, evecs_dev, s.nev, n, 1.0, 0.0, 0, s.st));
+    double mu_h[64], res_h[64];
+    int sel_h[64];
+    if (cudaMemcpyAsync(mu_h, s.b.mu, sizeof(double) * k, cudaMemcpyDeviceToHost, s.st) != cudaSuccess ||
+        cudaMemcpyAsync(sel_h, s.b.iflags + 8, sizeof(int) * s.nev, cudaMemcpyDeviceToHost, s.st) != cudaSuccess ||
+        cudaMemcpyAsync(res_h, s.b.res_sel, sizeof(double) * s.nev, cudaMemcpyDeviceToHost, s.st) != cudaSuccess ||
+        cudaStreamSynchronize(s.st) != cudaSuccess)
+        return MBL_ERR_CUDA;
+    double mx = 0.0;
+    for (int j = 0; j < s.nev; ++j) {
+        if (evals_host) evals_host[j] = sigma + mu_h[sel_h[j]];
+        if (resid_host) resid_host[j] = res_h[j];
+        mx = fmax(mx, res_h[j] / norm_h);
+    }
+    if (stats) {
+        stats->iters = it;
+        stats->converged = (status == MBL_OK) ? 1 : 0;
+        stats->matvecs = s.matvecs;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->max_rel_resid = mx;
+        stats->norm_h = norm_h;
+        stats->t_setup = s.tphase[9];
+        stats->t_resid = s.tphase[0];
+        stats->t_pcg = s.tphase[1];
+        stats->t_wp = s.tphase[2];
+        stats->t_gram = s.tphase[3];
+        stats->t_small = s.tphase[4];
+        stats->t_update = s.tphase[5];
+        stats->t_refresh = s.tphase[6];
+        stats->t_hrr = s.tphase[7];
+    }
+    if (s.timing)
+        for (auto &e : s.ev) cudaEventDestroy(e);
+    return status;
+}
+
+// ------------------------------------------------------------------------------------
+// Spectrum bounds.
+
+extern "C" int mbl_bounds_workspace_size(const mbl_chain *chain, int k, size_t *bytes)
+{
+    if (!chain || !bytes || k < 2 || k > 16) return MBL_ERR_ARG;
+    int64_t n = mbl_basis_size(chain->L, chain->n_up);
+    if (n <= 0 || (int64_t)3 * k > n) return MBL_ERR_ARG;
+    carve(nullptr, n, k, 1, bytes);
+    return MBL_OK;
+}
+
+static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, const double *X0, void *ws,
+                      size_t ws_bytes, int largest, double *theta_out, int *iters, cudaStream_t st)
+{
+    int64_t n = mbl_basis_size(chain->L, chain->n_up);
+    Solver s;
+    MBL_TRY(make_chain_params(chain, 0.0, &s.cp));
+    size_t need = 0;
+    s.b = carve((char *)ws, n, k, 1, &need);
+    if (ws_bytes < need) return MBL_ERR_WORKSPACE;
+    s.n = n;
+    s.k = k;
+    s.nev = 1;
+    s.m = 0;
+    s.mixed = 0;
+    s.largest = largest;
+    s.folded = 0;
+    s.pcg_tol = 0.0;
+    s.st = st;
+    if (cudaMemsetAsync(s.b.counter, 0, 4 * sizeof(unsigned), st) != cudaSuccess ||
+        cudaMemsetAsync(s.b.iflags, 0, (16 + 64) * sizeof(int), st) != cudaSuccess)
+        return MBL_ERR_CUDA;
+    MBL_TRY(mbl_basis_build(chain->L, chain->n_up, s.b.states, n, (mbl_stream_t)st));
+    s.cp.states = s.b.states;
+    MBL_TRY(s.cholqr_into_x(X0, k));
+    MBL_TRY(s.refresh_tx());
+    MBL_TRY(initial_rr(s));
+    MBL_TRY(s.enqueue_bounds_status());
+    bool have_p = false;
+    int it = 0;
+    double theta = 0.0, rn0 = 0.0;
+    for (;;) {
+        if (cudaMemcpyAsync(&theta, s.b.Gk, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&rn0, s.b.rn, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return MBL_ERR_CUDA;
+        if (!std::isfinite(theta) || !std::isfinite(rn0)) return MBL_ERR_NUMERIC;
+        if (rn0 <= tol * fabs(theta) || it >= max_iter) break;
+        MBL_TRY(s.enqueue_body(have_p));
+        have_p = true;
+        ++it;
+    }
+    *theta_out = theta;
+    if (iters) *iters += it;
+    return (rn0 <= tol * fabs(theta)) ? MBL_OK : MBL_ERR_NOT_CONVERGED;
+}
+
+extern "C" int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, int max_iter, const double *X0_dev,
+                                   void *workspace_dev, size_t workspace_bytes, double *emin_host, double *emax_host,
+                                   int *iters_host, mbl_stream_t stream)
+{
+    size_t need = 0;
+    int rc = mbl_bounds_workspace_size(chain, k, &need);
+    if (rc != MBL_OK) return rc;
+    if (!X0_dev || !workspace_dev || !(tol > 0.0) || max_iter < 0) return MBL_ERR_ARG;
+    if (workspace_bytes < need) return MBL_ERR_WORKSPACE;
+    ChainParams cp;
+    rc = make_chain_params(chain, 0.0, &cp);
+    if (rc != MBL_OK) return rc;
+    if (iters_host) *iters_host = 0;
+    double lo = 0.0, hi = 0.0;
+    int r1 = bounds_one(chain, k, tol, max_iter, X0_dev, workspace_dev, workspace_bytes, 0, &lo, iters_host,
+                        (cudaStream_t)stream);
+    if (r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) return r1;
+    int r2 = bounds_one(chain, k, tol, max_iter, X0_dev, workspace_dev, workspace_bytes, 1, &hi, iters_host,
+                        (cudaStream_t)stream);
+    if (r2 != MBL_OK && r2 != MBL_ERR_NOT_CONVERGED) return r2;
+    if (emin_host) *emin_host = lo;
+    if (emax_host) *emax_host = hi;
+    return (r1 == MBL_OK && r2 == MBL_OK) ? MBL_OK : MBL_ERR_NOT_CONVERGED;
+}

@@ -1,0 +1,542 @@
+// mbl_small.cu -- small dense kernels of the LOBPCG iteration (Sec. 3.2), each run by
+// one block: symmetric eigendecomposition by parallel cyclic Jacobi, Cholesky with
+// triangular inverse, the SVQB + Rayleigh-Ritz step on S = [X W P], and the selection
+// of the Ritz pairs nearest sigma.
+//
+// Precision.  GB300 executes FP64 at about 1/64 of its FP32 rate, so in mixed mode
+// the (3k x 3k) eigenproblems run in FP32 and only a k-dimensional refinement runs in
+// FP64: the k Ritz directions picked in FP32 are re-orthonormalised (Cholesky, FP64)
+// and a k x k Rayleigh-Ritz with the FP64 projection of A finishes the step.  The
+// convergence test (H Rayleigh-Ritz and residuals) is always FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "mbl_dense.h"
+
+namespace mbl {
+
+constexpr int kSmallThreads = 512;
+
+template <typename T>
+struct Eps;
+template <>
+struct Eps<float> {
+    static __device__ __forceinline__ float v() { return 1.2e-7f; }
+};
+template <>
+struct Eps<double> {
+    static __device__ __forceinline__ double v() { return 2.3e-16; }
+};
+
+// Parallel cyclic Jacobi on the symmetric n x n matrix A (row-major, ld n): the
+// round-robin (circle) ordering rotates n/2 disjoint pairs per round.  A rotation
+// zeroes a_pq with t = sign(tau)/(|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp)/(2 a_pq);
+// pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped.  On exit diag(A) holds the
+// eigenvalues and the columns of V the eigenvectors.  cs: n + 2 values, pairs: n + 2
+// ints (shared or global).
+template <typename T>
+__device__ void dev_jacobi(int n, T *A, T *V, T *cs, int *pairs, int *s_rot, int max_sweeps)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) V[e] = (e / n == e % n) ? (T)1 : (T)0;
+    __syncthreads();
+    if (n < 2) return;
+    const int np = (n + 1) & ~1;
+    const int half = np / 2;
+    const T eps = Eps<T>::v();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) *s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int i = tid; i < half; i += nt) {
+                int p, q;
+                if (i == 0) {
+                    p = round;
+                    q = np - 1;
+                } else {
+                    p = (round + i) % (np - 1);
+                    q = (round - i + (np - 1)) % (np - 1);
+                }
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                T c = (T)1, s = (T)0;
+                if (q < n) {
+                    const T apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
+                    if (apq != (T)0 && fabs(apq) > eps * sqrt(fabs(app * aqq))) {
+                        const T tau = (aqq - app) / ((T)2 * apq);
+                        const T t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+                        c = (T)1 / sqrt((T)1 + t * t);
+                        s = t * c;
+                        *s_rot = 1;
+                    }
+                }
+                pairs[2 * i] = p;
+                pairs[2 * i + 1] = q;
+                cs[2 * i] = c;
+                cs[2 * i + 1] = s;
+            }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += nt) {
+                const int i = e / n, j = e % n;
+                const T s = cs[2 * i + 1];
+                if (s == (T)0) continue;
+                const int p = pairs[2 * i], q = pairs[2 * i + 1];
+                const T c = cs[2 * i];
+                const T ap = A[p * n + j], aq = A[q * n + j];
+                A[p * n + j] = c * ap - s * aq;
+                A[q * n + j] = s * ap + c * aq;
+            }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += nt) {
+                const int i = e / n, j = e % n;
+                const T s = cs[2 * i + 1];
+                if (s == (T)0) continue;
+                const int p = pairs[2 * i], q = pairs[2 * i + 1];
+                const T c = cs[2 * i];
+                const T ap = A[j * n + p], aq = A[j * n + q];
+                A[j * n + p] = c * ap - s * aq;
+                A[j * n + q] = s * ap + c * aq;
+                const T vp = V[j * n + p], vq = V[j * n + q];
+                V[j * n + p] = c * vp - s * vq;
+                V[j * n + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+        const int rot = *s_rot;
+        __syncthreads();
+        if (!rot) break;
+    }
+}
+
+// Ascending sort of the eigenpairs left by dev_jacobi: w[rank] = A[j][j],
+// Vs[:, rank] = V[:, j] (Vs ld n).
+template <typename T, typename TO>
+__device__ void dev_sort_eig(int n, const T *A, const T *V, TO *w, TO *Vs)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = tid; j < n; j += nt) {
+        const T lj = A[j * n + j];
+        int rank = 0;
+        for (int i = 0; i < n; ++i) {
+            const T li = A[i * n + i];
+            if (li < lj || (li == lj && i < j)) ++rank;
+        }
+        w[rank] = (TO)lj;
+        for (int i = 0; i < n; ++i) Vs[i * n + rank] = (TO)V[i * n + j];
+    }
+    __syncthreads();
+}
+
+// Upper Cholesky G = R^T R of the symmetric part of G (n x n, ld ldg) and Rinv = R^-1.
+// Returns 1 (in every thread) when a pivot is not positive and finite; Rinv is then I.
+__device__ int dev_chol_inv(int n, const double *G, int ldg, double *R, double *Rinv, int *s_flag)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) *s_flag = 0;
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, j = e % n;
+        R[e] = (j >= i) ? 0.5 * (G[i * ldg + j] + G[j * ldg + i]) : 0.0;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < n; ++kk) {
+        if (tid == 0) {
+            const double d = R[kk * n + kk];
+            double pv = 1.0;
+            if (!(d > 0.0) || !isfinite(d)) *s_flag = 1;
+            else pv = sqrt(d);
+            R[kk * n + kk] = pv;
+        }
+        __syncthreads();
+        const double piv = R[kk * n + kk];
+        for (int j = kk + 1 + tid; j < n; j += nt) R[kk * n + j] /= piv;
+        __syncthreads();
+        const int m = n - kk - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = kk + 1 + e / m, j = kk + 1 + e % m;
+            if (j >= i) R[i * n + j] -= R[kk * n + i] * R[kk * n + j];
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < n; j += nt) {
+        for (int i = n - 1; i >= 0; --i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int m = i + 1; m <= j; ++m) s -= R[i * n + m] * Rinv[m * n + j];
+            Rinv[i * n + j] = (i <= j) ? s / R[i * n + i] : 0.0;
+        }
+    }
+    __syncthreads();
+    const int bad = *s_flag;
+    if (bad)
+        for (int e = tid; e < n * n; e += nt) Rinv[e] = (e / n == e % n) ? 1.0 : 0.0;
+    __syncthreads();
+    return bad;
+}
+
+// ---------------------------------------------------------------------------------
+// Symmetric eigendecomposition (FP64 Jacobi) of G (n x n, ld ldg): w ascending, Z
+// (n x n) eigenvectors in columns.  A and V live in shared memory when they fit.
+__global__ void __launch_bounds__(kSmallThreads) k_small_eig(int n, const double *G, int64_t ldg, double *w,
+                                                             double *Z, double *work, int in_smem)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_rot;
+    double *A = in_smem ? reinterpret_cast<double *>(smem_raw) : work;
+    double *V = A + n * n;
+    double *cs = in_smem ? V + n * n : work + 2 * n * n;
+    int *pairs = reinterpret_cast<int *>(cs + n + 2);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        A[e] = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
+    }
+    __syncthreads();
+    dev_jacobi<double>(n, A, V, cs, pairs, &s_rot, 40);
+    dev_sort_eig<double, double>(n, A, V, w, Z);
+}
+
+static size_t eig_smem_bytes(int n) { return (size_t)(2 * n * n + 2 * n + 8) * sizeof(double); }
+
+size_t small_eig_work_doubles(int n) { return (size_t)2 * n * n + 2 * n + 8; }
+
+int small_eig(int n, const double *G, int64_t ldg, double *w, double *Z, double *work, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_small_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_smem_bytes(64));
+        attr = true;
+    }
+    const int in_smem = n <= 64;
+    k_small_eig<<<1, kSmallThreads, in_smem ? eig_smem_bytes(n) : 0, st>>>(n, G, ldg, w, Z, work, in_smem);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_small_chol_inv(int n, const double *G, int64_t ldg, double *Rinv,
+                                                                  double *work, int *flag)
+{
+    __shared__ int s_flag;
+    const int bad = dev_chol_inv(n, G, (int)ldg, work, Rinv, &s_flag);
+    if (threadIdx.x == 0) *flag = bad;
+}
+
+int small_chol_inv(int n, const double *G, int64_t ldg, double *Rinv, double *work, int *flag, cudaStream_t st)
+{
+    k_small_chol_inv<<<1, kSmallThreads, 0, st>>>(n, G, ldg, Rinv, work, flag);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------
+// SVQB + Rayleigh-Ritz on span(S), S = [X W P] with w columns (Stathopoulos & Wu):
+//   D = diag(G_S)^-1/2, eig(D G_S D) = U L U^T, keep L_i > tau max L,
+//   C_S = D U_keep L_keep^-1/2, eig(C_S^T G_A C_S) = Z theta,
+//   coef = C_S Z[:, first k]  (the k smallest; the k largest, descending, if 'largest').
+// T is the precision of the two eigensolves.  With T = float a k-dimensional FP64
+// refinement follows: Y = C_S Z_k, Y <- Y R^-1 with R^T R = Z_k^T Z_k, M = Y^T G_A Y,
+// eig(M) = Q mu (FP64), coef = Y Q.
+// info[0] = kept directions, info[1] = 1 on NaN/Inf or a failed refinement.
+
+size_t small_rr_work_doubles(int w) { return (size_t)12 * w * w + 16 * w + 64; }
+
+template <typename T>
+__device__ void rr_body(int w, int k, int largest, const double *GS, const double *GA, double tau, double *coef,
+                        double *theta, double *work, int *info, T *As, T *Vs, int use_smem)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int s_rot, s_keep, s_first, s_flag;
+    // carve the FP64 workspace
+    double *dsc = work;                  // w
+    double *lam = dsc + w;               // w
+    double *Cs = lam + w;                // w x w (ld w; keep columns used)
+    T *U = reinterpret_cast<T *>(Cs + w * w);  // w x w
+    T *T2 = U + w * w;                   // w x w
+    T *Z = T2 + w * w;                   // w x w (keep x keep, ld keep)
+    T *csb = Z + w * w;                  // w + 2
+    int *pairs = reinterpret_cast<int *>(csb + w + 2);  // w + 2
+    double *dbase = reinterpret_cast<double *>(pairs + w + 4);
+    dbase = reinterpret_cast<double *>(((uintptr_t)dbase + 15) & ~(uintptr_t)15);
+    double *Zk = dbase;                  // keep x k
+    double *Y = Zk + w * k;              // w x k
+    double *B = Y + w * k;               // w x k
+    double *M = B + w * k;               // k x k
+    double *R = M + k * k;               // k x k
+    double *Ri = R + k * k;              // k x k
+    double *Q = Ri + k * k;              // k x k
+    double *mu = Q + k * k;              // k
+    double *A64 = mu + k;                // k x k
+    double *V64 = A64 + k * k;           // k x k
+    double *cs64 = V64 + k * k;          // k + 2
+    int *pairs64 = reinterpret_cast<int *>(cs64 + k + 2);
+    T *Ag = reinterpret_cast<T *>(((uintptr_t)(pairs64 + k + 8) + 15) & ~(uintptr_t)15);
+    T *A = use_smem ? As : Ag;
+    T *V = use_smem ? Vs : Ag + w * w;
+
+    for (int i = tid; i < w; i += nt) {
+        const double d = GS[i * w + i];
+        dsc[i] = (d > 0.0 && isfinite(d)) ? 1.0 / sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < w * w; e += nt) {
+        const int i = e / w, j = e % w;
+        A[e] = (T)(dsc[i] * 0.5 * (GS[i * w + j] + GS[j * w + i]) * dsc[j]);
+    }
+    __syncthreads();
+    dev_jacobi<T>(w, A, V, csb, pairs, &s_rot, 40);
+    dev_sort_eig<T, T>(w, A, V, reinterpret_cast<T *>(lam), U);
+    if (tid == 0) {
+        const T *lt = reinterpret_cast<const T *>(lam);
+        const double lmax = (double)lt[w - 1];
+        int first = w;
+        for (int i = 0; i < w; ++i)
+            if ((double)lt[i] > tau * lmax) {
+                first = i;
+                break;
+            }
+        s_first = first;
+        s_keep = w - first;
+    }
+    __syncthreads();
+    const int first = s_first, keep = s_keep;
+    {
+        const T *lt = reinterpret_cast<const T *>(lam);
+        for (int e = tid; e < w * keep; e += nt) {
+            const int i = e / keep, j = e % keep;
+            Cs[i * w + j] = dsc[i] * (double)U[i * w + first + j] / sqrt((double)lt[first + j]);
+        }
+    }
+    __syncthreads();
+    // T2 = G_A Cs (w x keep) and A = Cs^T T2 (keep x keep, ld keep), in precision T
+    for (int e = tid; e < w * keep; e += nt) {
+        const int i = e / keep, j = e % keep;
+        T s = (T)0;
+        for (int m = 0; m < w; ++m) s += (T)(0.5 * (GA[i * w + m] + GA[m * w + i])) * (T)Cs[m * w + j];
+        T2[i * w + j] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < keep * keep; e += nt) {
+        const int i = e / keep, j = e % keep;
+        T s = (T)0;
+        for (int m = 0; m < w; ++m) s += (T)Cs[m * w + i] * T2[m * w + j];
+        A[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < keep * keep; e += nt) {
+        const int i = e / keep, j = e % keep;
+        if (i < j) {
+            const T a = (T)0.5 * (A[i * keep + j] + A[j * keep + i]);
+            A[i * keep + j] = a;
+            A[j * keep + i] = a;
+        }
+    }
+    __syncthreads();
+    dev_jacobi<T>(keep, A, V, csb, pairs, &s_rot, 40);
+    T *lam2 = reinterpret_cast<T *>(lam);
+    dev_sort_eig<T, T>(keep, A, V, lam2, Z);
+    const int kk = k < keep ? k : keep;
+    if (sizeof(T) == sizeof(double)) {
+        for (int e = tid; e < w * k; e += nt) {
+            const int i = e / k, j = e % k;
+            double s = 0.0;
+            if (j < kk) {
+                const int col = largest ? keep - 1 - j : j;
+                for (int m = 0; m < keep; ++m) s += Cs[i * w + m] * (double)Z[m * keep + col];
+            }
+            coef[e] = s;
+        }
+        for (int j = tid; j < k; j += nt) theta[j] = j < kk ? (double)lam2[largest ? keep - 1 - j : j] : 0.0;
+        if (tid == 0) {
+            info[0] = keep;
+            int bad = 0;
+            for (int j = 0; j < kk; ++j)
+                if (!isfinite((double)lam2[j])) bad = 1;
+            info[1] = bad;
+        }
+        return;
+    }
+    // FP64 refinement of the k-dimensional Ritz subspace
+    for (int e = tid; e < keep * kk; e += nt) {
+        const int i = e / kk, j = e % kk;
+        Zk[e] = (double)Z[i * keep + (largest ? keep - 1 - j : j)];
+    }
+    __syncthreads();
+    for (int e = tid; e < kk * kk; e += nt) {  // M = Zk^T Zk
+        const int i = e / kk, j = e % kk;
+        double s = 0.0;
+        for (int m = 0; m < keep; ++m) s += Zk[m * kk + i] * Zk[m * kk + j];
+        M[e] = s;
+    }
+    __syncthreads();
+    const int bad_chol = dev_chol_inv(kk, M, kk, R, Ri, &s_flag);
+    for (int e = tid; e < keep * kk; e += nt) {  // B <- Zk Ri (keep x kk), B as scratch
+        const int i = e / kk, j = e % kk;
+        double s = 0.0;
+        for (int l = 0; l <= j; ++l) s += Zk[i * kk + l] * Ri[l * kk + j];
+        B[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < w * kk; e += nt) {  // Y = Cs (Zk Ri)
+        const int i = e / kk, j = e % kk;
+        double s = 0.0;
+        for (int m = 0; m < keep; ++m) s += Cs[i * w + m] * B[m * kk + j];
+        Y[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < w * kk; e += nt) {  // B = G_A Y
+        const int i = e / kk, j = e % kk;
+        double s = 0.0;
+        for (int m = 0; m < w; ++m) s += 0.5 * (GA[i * w + m] + GA[m * w + i]) * Y[m * kk + j];
+        B[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < kk * kk; e += nt) {  // A64 = Y^T B
+        const int i = e / kk, j = e % kk;
+        double s = 0.0;
+        for (int m = 0; m < w; ++m) s += Y[m * kk + i] * B[m * kk + j];
+        A64[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < kk * kk; e += nt) {
+        const int i = e / kk, j = e % kk;
+        if (i < j) {
+            const double a = 0.5 * (A64[i * kk + j] + A64[j * kk + i]);
+            A64[i * kk + j] = a;
+            A64[j * kk + i] = a;
+        }
+    }
+    __syncthreads();
+    dev_jacobi<double>(kk, A64, V64, cs64, pairs64, &s_rot, 40);
+    dev_sort_eig<double, double>(kk, A64, V64, mu, Q);
+    for (int e = tid; e < w * k; e += nt) {  // coef = Y Q (descending for 'largest')
+        const int i = e / k, j = e % k;
+        double s = 0.0;
+        if (j < kk) {
+            const int col = largest ? kk - 1 - j : j;
+            for (int m = 0; m < kk; ++m) s += Y[i * kk + m] * Q[m * kk + col];
+        }
+        coef[e] = s;
+    }
+    for (int j = tid; j < k; j += nt) theta[j] = j < kk ? mu[largest ? kk - 1 - j : j] : 0.0;
+    if (tid == 0) {
+        info[0] = keep;
+        int bad = bad_chol;
+        for (int j = 0; j < kk; ++j)
+            if (!isfinite(mu[j])) bad = 1;
+        info[1] = bad;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) k_small_rr(int w, int k, int largest, const double *GS,
+                                                            const double *GA, double tau, double *coef,
+                                                            double *theta, double *work, int *info, int use_smem)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Vs = As + w * w;
+    rr_body<T>(w, k, largest, GS, GA, tau, coef, theta, work, info, As, Vs, use_smem);
+}
+
+int small_svqb_rr(int w, int k, int largest, int mixed, const double *GS, const double *GA, double tau,
+                  double *coef, double *theta, double *work, int *info, cudaStream_t st)
+{
+    static bool attr = false;
+    const int cap = 160 * 1024;
+    if (!attr) {
+        cudaFuncSetAttribute(k_small_rr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+        cudaFuncSetAttribute(k_small_rr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+        attr = true;
+    }
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    const size_t sm = 2 * (size_t)w * w * es;
+    const int use_smem = sm <= (size_t)cap;
+    if (mixed)
+        k_small_rr<float><<<1, kSmallThreads, use_smem ? sm : 0, st>>>(w, k, largest, GS, GA, tau, coef, theta,
+                                                                       work, info, use_smem);
+    else
+        k_small_rr<double><<<1, kSmallThreads, use_smem ? sm : 0, st>>>(w, k, largest, GS, GA, tau, coef, theta,
+                                                                        work, info, use_smem);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------
+// Rayleigh-Ritz with H on span(X) for the convergence test and the final extraction.
+// In: mu, V = eig(M), M = X^T (H - sigma) X; EtE = E^T E, E = (H - sigma)X - X M.
+// Residual of pair j: sqrt(v_j^T EtE v_j).  Selects the nev values of mu nearest 0
+// (ties: lower first), writes sel (ascending mu), res_sel, st[0] = converged,
+// st[1] = NaN/Inf seen, dst[0] = max relative residual of the selection.
+__global__ void k_hrr_select(int k, int nev, const double *mu, const double *V, const double *EtE, double tol_abs,
+                             double norm_h, double *res_all, int *sel, double *res_sel, int *st, double *dst)
+{
+    const int tid = threadIdx.x;
+    for (int j = tid; j < k; j += blockDim.x) {
+        double s = 0.0;
+        for (int a = 0; a < k; ++a) {
+            double t = 0.0;
+            for (int b = 0; b < k; ++b) t += 0.5 * (EtE[a * k + b] + EtE[b * k + a]) * V[b * k + j];
+            s += V[a * k + j] * t;
+        }
+        res_all[j] = sqrt(fmax(s, 0.0));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int chosen[64];
+        int nc = 0;
+        for (int t = 0; t < nev; ++t) {
+            int best = -1;
+            for (int j = 0; j < k; ++j) {
+                bool used = false;
+                for (int u = 0; u < nc; ++u)
+                    if (chosen[u] == j) used = true;
+                if (used) continue;
+                if (best < 0 || fabs(mu[j]) < fabs(mu[best]) || (fabs(mu[j]) == fabs(mu[best]) && mu[j] < mu[best]))
+                    best = j;
+            }
+            chosen[nc++] = best;
+        }
+        for (int a = 0; a < nc; ++a)
+            for (int b = a + 1; b < nc; ++b)
+                if (chosen[b] < chosen[a]) {
+                    const int t = chosen[a];
+                    chosen[a] = chosen[b];
+                    chosen[b] = t;
+                }
+        int conv = 1, bad = 0;
+        double mx = 0.0;
+        for (int a = 0; a < nc; ++a) {
+            const double r = res_all[chosen[a]];
+            sel[a] = chosen[a];
+            res_sel[a] = r;
+            if (!isfinite(r) || !isfinite(mu[chosen[a]])) bad = 1;
+            if (!(r <= tol_abs)) conv = 0;
+            mx = fmax(mx, r / norm_h);
+        }
+        st[0] = conv;
+        st[1] = bad;
+        dst[0] = mx;
+    }
+}
+
+int hrr_select(int k, int nev, const double *mu, const double *V, const double *EtE, double tol_abs, double norm_h,
+               double *res_all, int *sel, double *res_sel, int *st, double *dst, cudaStream_t s)
+{
+    k_hrr_select<<<1, 64, 0, s>>>(k, nev, mu, V, EtE, tol_abs, norm_h, res_all, sel, res_sel, st, dst);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+// Csel (k x nev) = V[:, sel]
+__global__ void k_gather_cols(int k, int nev, const double *V, const int *sel, double *Csel)
+{
+    for (int e = threadIdx.x; e < k * nev; e += blockDim.x) {
+        const int i = e / nev, j = e % nev;
+        Csel[e] = V[i * k + sel[j]];
+    }
+}
+
+int gather_cols(int k, int nev, const double *V, const int *sel, double *Csel, cudaStream_t st)
+{
+    k_gather_cols<<<1, 256, 0, st>>>(k, nev, V, sel, Csel);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+}  // namespace mbl

@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA library (through the C ABI) against the oracle.
+
+Integer work (basis, ranks) must match bit for bit.  Products must match the FP64
+oracle within a bound derived from the arithmetic: each output element is a sum of
+at most |B| + 1 rounded terms, so its error is at most c * u * (|d - sigma| |x_r| +
+1/2 sum |x_r'|) with u the unit roundoff of the kernel's type, plus (FP32 only) the
+rounding of d - sigma itself, |d_err| <= 6 u32 (sum|h| + |sigma| + delta |B| / 2).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import hamiltonian as ham
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mbl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2012_00217_gb300 as m
+    m.binding.lib()
+    return m
+
+
+def _gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+# ---------------------------------------------------------------- basis
+@pytest.mark.parametrize("L,n_up", [(2, 1), (5, 2), (12, 6), (12, 0), (12, 12), (13, 4), (16, 8),
+                                    (20, 10), (24, 12), (25, 9)])
+def test_basis_build_bit_exact(mbl, L, n_up):
+    ref = ham.basis(L, n_up)
+    n = mbl.basis_size(L, n_up)
+    assert n == ref.size
+    st = torch.empty(n, dtype=torch.int32, device=DEV)
+    mbl.basis_build(L, n_up, st)
+    got = st.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("L,n_up", [(12, 6), (18, 9), (26, 13), (28, 14), (32, 16)])
+def test_basis_rank_bit_exact(mbl, L, n_up):
+    rng = np.random.default_rng(L)
+    # valid words from random rank positions (built on the GPU, ranked back) and
+    # random words (mostly invalid)
+    n = mbl.basis_size(L, n_up)
+    q = 200000 if L <= 28 else 20000
+    pos = rng.integers(0, n, q)
+    words_valid = np.empty(q, dtype=np.uint32)
+    # unrank on the CPU by the definition for L <= 24, else via the GPU basis for L <= 28
+    if L <= 28:
+        st = torch.empty(n, dtype=torch.int32, device=DEV)
+        mbl.basis_build(L, n_up, st)
+        words_valid = st.cpu().numpy().view(np.uint32)[pos]
+    else:
+        # popcount-n_up words drawn directly
+        for i in range(q):
+            bits = rng.choice(L, n_up, replace=False)
+            words_valid[i] = np.sum(np.uint64(1) << bits.astype(np.uint64)).astype(np.uint32)
+    words_rand = rng.integers(0, 2 ** 32, q, dtype=np.uint64).astype(np.uint32)
+    words = np.concatenate([words_valid, words_rand])
+    ranks = torch.empty(words.size, dtype=torch.int64, device=DEV)
+    mbl.basis_rank(L, n_up, _gpu(words.view(np.int32)), ranks)
+    got = ranks.cpu().numpy()
+    if L <= 28:
+        assert np.array_equal(got[:q], pos)
+    # reference for every word: popcount / range check, then the combinatorial sum
+    from math import comb
+    pc = np.array([bin(int(w)).count("1") for w in words])
+    inr = (words.astype(np.uint64) >> np.uint64(L)) == 0 if L < 32 else np.ones(words.size, bool)
+    valid = (pc == n_up) & inr
+    assert np.all(got[~valid] == -1)
+    sample = np.nonzero(valid)[0][:2000]
+    for i in sample:
+        w, r, j = int(words[i]), 0, 0
+        for p in range(32):
+            if (w >> p) & 1:
+                j += 1
+                r += comb(p, j)
+        assert got[i] == r
+
+
+# ---------------------------------------------------------------- product
+def _offdiag_abs(chain, X):
+    """1/2 sum over neighbours of |x_r'|, via the oracle with zero diagonal."""
+    c0 = ham.Chain(chain.L, np.zeros(chain.L), delta=0.0, periodic=chain.periodic, n_up=chain.n_up)
+    return ham.apply(c0, 0.0, np.abs(X).astype(np.float64))
+
+
+def _bound(chain, sigma, X, dtype):
+    d = ham.diag(chain) - sigma
+    scale = np.abs(d)[:, None] * np.abs(X.astype(np.float64)) + _offdiag_abs(chain, X)
+    nb = chain.num_bonds()
+    u = np.finfo(dtype).eps
+    derr = 6 * u * (np.sum(np.abs(chain.h)) + abs(sigma) + chain.delta * nb / 2 + 1)
+    return 4 * (nb + 2) * u * scale + derr * np.abs(X.astype(np.float64)) + 1e-300
+
+
+CASES = [(10, False, 1.0), (13, True, 0.7), (16, True, 1.0), (18, False, 0.0), (14, False, 1.0)]
+
+
+@pytest.mark.parametrize("L,periodic,delta", CASES)
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_apply_matches_oracle(mbl, L, periodic, delta, k, dtype):
+    h = wl.fields(L, 8.0, L + k)
+    chain = ham.Chain(L, h, delta=delta, periodic=periodic)
+    n = ham.sector_dim(L, L // 2)
+    X = wl.block(n, k, 100 + k, dtype)
+    sigma = 0.37
+    ref = ham.apply(chain, sigma, X.astype(np.float64))
+    Y = torch.empty((n, k), dtype=torch.float32 if dtype == np.float32 else torch.float64, device=DEV)
+    mbl.hamiltonian_apply(mbl.make_chain(L, h, delta, periodic), sigma, _gpu(X), Y)
+    got = Y.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    assert np.all(err <= _bound(chain, sigma, X, dtype)), err.max()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_apply_strided_and_odd_sectors(mbl, dtype):
+    """Leading dimensions > k, a sector away from half filling, and a ragged k."""
+    for (L, n_up, periodic, k, ld) in [(13, 5, True, 8, 12), (12, 3, False, 5, 7), (11, 6, True, 32, 40),
+                                       (2, 1, False, 4, 4), (9, 0, True, 3, 3), (8, 8, False, 2, 2)]:
+        h = wl.fields(L, 4.0, L * 7 + n_up)
+        chain = ham.Chain(L, h, delta=0.9, periodic=periodic, n_up=n_up)
+        n = ham.sector_dim(L, n_up)
+        Xb = wl.block(n, ld, 7, dtype)
+        ref = ham.apply(chain, -0.2, Xb[:, :k].astype(np.float64))
+        Yb = torch.full((n, ld), 123.0, dtype=torch.float32 if dtype == np.float32 else torch.float64, device=DEV)
+        Xt = _gpu(Xb)
+        mbl.hamiltonian_apply(mbl.make_chain(L, h, 0.9, periodic, n_up), -0.2, Xt[:, :k], Yb[:, :k])
+        got = Yb.cpu().numpy()
+        assert np.all(got[:, k:] == 123.0)  # untouched padding
+        err = np.abs(got[:, :k].astype(np.float64) - ref)
+        assert np.all(err <= _bound(chain, -0.2, Xb[:, :k], dtype))
+
+
+def test_apply_deterministic(mbl):
+    L, k = 18, 32
+    h = wl.fields(L, 8.0, 3)
+    n = ham.sector_dim(L, L // 2)
+    X = _gpu(wl.block(n, k, 9, np.float32))
+    c = mbl.make_chain(L, h, 1.0, True)
+    Y1 = torch.empty_like(X)
+    Y2 = torch.empty_like(X)
+    mbl.hamiltonian_apply(c, 0.1, X, Y1)
+    mbl.hamiltonian_apply(c, 0.1, X, Y2)
+    assert torch.equal(Y1, Y2)
+
+
+def test_apply_rejects_bad_arguments(mbl):
+    L = 10
+    h = wl.fields(L, 1.0, 0)
+    n = ham.sector_dim(L, 5)
+    X = torch.zeros((n, 4), dtype=torch.float64, device=DEV)
+    Y = torch.zeros_like(X)
+    with pytest.raises(mbl.MBLError):  # wrong n
+        mbl.hamiltonian_apply(mbl.make_chain(L, h, 1.0, False, 4), 0.0, X, Y)
+    with pytest.raises(mbl.MBLError):  # in-place
+        mbl.hamiltonian_apply(mbl.make_chain(L, h), 0.0, X, X)
+    hn = h.copy()
+    hn[3] = np.nan
+    with pytest.raises(mbl.MBLError):
+        mbl.hamiltonian_apply(mbl.make_chain(L, hn), 0.0, X, Y)
+
+
+@pytest.mark.parametrize("L,k,dtype", [(26, 8, np.float32), (26, 64, np.float32), (24, 32, np.float64),
+                                       (28, 16, np.float32)])
+def test_apply_full_size_sampled(mbl, L, k, dtype):
+    """Full-size sweep shapes: sampled rows against the oracle row product."""
+    h = wl.fields(L, 8.0, 0)
+    chain = ham.Chain(L, h, periodic=False)
+    n = ham.sector_dim(L, L // 2)
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    g = torch.Generator(device=DEV)
+    g.manual_seed(L * 100 + k)
+    X = torch.randn((n, k), generator=g, device=DEV, dtype=tdt)
+    Y = torch.empty_like(X)
+    mbl.hamiltonian_apply(mbl.make_chain(L, h), 0.5, X, Y)
+    rng = np.random.default_rng(k)
+    rows = np.unique(np.concatenate([rng.integers(0, n, 300), [0, 1, n // 2, n - 2, n - 1]]))
+    # the oracle needs every neighbour row of the sampled rows: copy X back once
+    Xh = X.cpu().numpy()
+    ref = ham.apply_rows(chain, 0.5, Xh.astype(np.float64), rows)
+    got = Y[torch.from_numpy(rows).to(DEV)].cpu().numpy().astype(np.float64)
+    d = ham.diag(chain)[rows] - 0.5
+    u = np.finfo(dtype).eps
+    scale = (np.abs(d)[:, None] + 0.5 * L) * np.abs(Xh).max()
+    derr = 6 * u * (np.sum(np.abs(h)) + 0.5 + L)
+    assert np.all(np.abs(got - ref) <= 4 * (L + 2) * u * scale + derr * np.abs(Xh).max())
