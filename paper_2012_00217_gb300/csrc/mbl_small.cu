@@ -17,6 +17,7 @@
 namespace mbl {
 
 constexpr int kSmallThreads = 512;
+constexpr int kMaxSweeps = 20;
 
 template <typename T>
 struct Eps;
@@ -32,7 +33,9 @@ struct Eps<double> {
 // Parallel cyclic Jacobi on the symmetric n x n matrix A (row-major, ld n): the
 // round-robin (circle) ordering rotates n/2 disjoint pairs per round.  A rotation
 // zeroes a_pq with t = sign(tau)/(|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp)/(2 a_pq);
-// pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped.  On exit diag(A) holds the
+// pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped (the relative test keeps the
+// small eigenvalues of graded matrices accurate), and the sweeps stop when a sweep
+// rotates nothing or after max_sweeps.  On exit diag(A) holds the
 // eigenvalues and the columns of V the eigenvectors.  cs: n + 2 values, pairs: n + 2
 // ints (shared or global).
 template <typename T>
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_eig(int n, const double
         A[e] = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
     }
     __syncthreads();
-    dev_jacobi<double>(n, A, V, cs, pairs, &s_rot, 40);
+    dev_jacobi<double>(n, A, V, cs, pairs, &s_rot, kMaxSweeps);
     dev_sort_eig<double, double>(n, A, V, w, Z);
 }
 
@@ -282,7 +285,7 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
         A[e] = (T)(dsc[i] * 0.5 * (GS[i * w + j] + GS[j * w + i]) * dsc[j]);
     }
     __syncthreads();
-    dev_jacobi<T>(w, A, V, csb, pairs, &s_rot, 40);
+    dev_jacobi<T>(w, A, V, csb, pairs, &s_rot, kMaxSweeps);
     dev_sort_eig<T, T>(w, A, V, reinterpret_cast<T *>(lam), U);
     if (tid == 0) {
         const T *lt = reinterpret_cast<const T *>(lam);
@@ -330,7 +333,7 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
         }
     }
     __syncthreads();
-    dev_jacobi<T>(keep, A, V, csb, pairs, &s_rot, 40);
+    dev_jacobi<T>(keep, A, V, csb, pairs, &s_rot, kMaxSweeps);
     T *lam2 = reinterpret_cast<T *>(lam);
     dev_sort_eig<T, T>(keep, A, V, lam2, Z);
     const int kk = k < keep ? k : keep;
@@ -405,7 +408,7 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
         }
     }
     __syncthreads();
-    dev_jacobi<double>(kk, A64, V64, cs64, pairs64, &s_rot, 40);
+    dev_jacobi<double>(kk, A64, V64, cs64, pairs64, &s_rot, kMaxSweeps);
     dev_sort_eig<double, double>(kk, A64, V64, mu, Q);
     for (int e = tid; e < w * k; e += nt) {  // coef = Y Q (descending for 'largest')
         const int i = e / k, j = e % k;
