@@ -146,6 +146,27 @@ int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts
                      double *evals_host, double *evecs_dev, double *resid_host,
                      mbl_lobpcg_stats *stats, mbl_stream_t stream);
 
+/* Same solve for callers that cannot allocate device memory: code running while a
+ * stream is being captured into a CUDA graph (where an allocation would be recorded into
+ * the graph or fail), plug-ins whose host application's own allocator owns the device
+ * memory pool, and real-time callers with a fixed memory budget decided up front.  The
+ * paper has no counterpart; this entry point only changes where the workspace lives.
+ * The workspace is one fixed device array of MBL_NOALLOC_SCRATCH_BYTES (16 MiB) inside
+ * the library, present on every GPU that loads the library until the process exits;
+ * problems whose mbl_lobpcg_workspace_size exceeds it are rejected with
+ * MBL_ERR_WORKSPACE before anything is launched (16 MiB covers, for instance, L = 12 with
+ * k <= 64, L = 14 with k <= 32 and L = 16 with k = 8).  The call allocates nothing: no cudaMalloc or cudaFree,
+ * no graph instantiation (opts->use_graph is ignored) and no timing events
+ * (opts->timing is ignored).  The first call on a device looks up the array's device
+ * address with that device current.  Every call shares the one array and leaves its
+ * contents behind; the solver clears what must start at zero.  Calls whose work overlaps
+ * on the GPU (other streams, other host threads) race on the array: serialise them.
+ * Arguments and results are those of mbl_lobpcg_solve. */
+#define MBL_NOALLOC_SCRATCH_BYTES (16u << 20)
+int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
+                             const double *X0_dev, double *evals_host, double *evecs_dev,
+                             double *resid_host, mbl_lobpcg_stats *stats, mbl_stream_t stream);
+
 /* Spectrum bounds E_min, E_max of the sector Hamiltonian (used to place sigma at the
  * middle of the spectrum and to scale tolerances): unpreconditioned LOBPCG on +H and
  * on -H, block width k (2 <= k <= 16), stopping when the lowest Ritz pair has

@@ -30,7 +30,8 @@ MODE_MIXED = 1
 
 EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis_rank",
             "mbl_hamiltonian_apply", "mbl_lobpcg_workspace_size", "mbl_lobpcg_solve",
-            "mbl_bounds_workspace_size", "mbl_spectrum_bounds")
+            "mbl_bounds_workspace_size", "mbl_spectrum_bounds", "mbl_lobpcg_solve_noalloc")
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class MBLError(RuntimeError):
@@ -85,6 +86,8 @@ def lib():
     so.mbl_lobpcg_workspace_size.argtypes = [pch, popt, ctypes.POINTER(sz)]
     so.mbl_lobpcg_solve.restype = i32
     so.mbl_lobpcg_solve.argtypes = [pch, f64, popt, p, p, sz, p, p, p, ctypes.POINTER(LobpcgStats), p]
+    so.mbl_lobpcg_solve_noalloc.restype = i32
+    so.mbl_lobpcg_solve_noalloc.argtypes = [pch, f64, popt, p, p, p, p, ctypes.POINTER(LobpcgStats), p]
     so.mbl_bounds_workspace_size.restype = i32
     so.mbl_bounds_workspace_size.argtypes = [pch, i32, ctypes.POINTER(sz)]
     so.mbl_spectrum_bounds.restype = i32
@@ -207,6 +210,29 @@ def lobpcg_solve(chain, sigma, opts, X0, workspace, evecs=None, allow_not_conver
                                 resid.ctypes.data_as(ctypes.c_void_p), ctypes.byref(stats),
                                 _stream_ptr(X0))
     _check(rc, "mbl_lobpcg_solve", ok)
+    return evals, resid, stats.as_dict(), rc
+
+
+def lobpcg_solve_noalloc(chain, sigma, opts, X0, evecs=None, allow_not_converged=False):
+    """mbl_lobpcg_solve_noalloc: the same solve with the library's fixed in-device
+    workspace (no allocation by the library or by this wrapper's callee).  Returns
+    (evals, resid, stats dict, status)."""
+    torch = _torch()
+    nev = opts.nev
+    evals = np.zeros(nev, dtype=np.float64)
+    resid = np.zeros(nev, dtype=np.float64)
+    stats = LobpcgStats()
+    ev_ptr = _dev(evecs, torch.float64, "evecs") if evecs is not None else None
+    if evecs is not None and (evecs.shape != (X0.shape[0], nev) or not evecs.is_contiguous()):
+        raise ValueError("evecs must be a contiguous n x nev tensor")
+    if not X0.is_contiguous() or X0.dim() != 2 or X0.shape[1] != opts.k:
+        raise ValueError("X0 must be a contiguous n x k tensor")
+    ok = (MBL_OK, MBL_ERR_NOT_CONVERGED) if allow_not_converged else (MBL_OK,)
+    rc = lib().mbl_lobpcg_solve_noalloc(ctypes.byref(chain), float(sigma), ctypes.byref(opts),
+                                        _dev(X0, torch.float64, "X0"), evals.ctypes.data_as(ctypes.c_void_p),
+                                        ev_ptr, resid.ctypes.data_as(ctypes.c_void_p), ctypes.byref(stats),
+                                        _stream_ptr(X0))
+    _check(rc, "mbl_lobpcg_solve_noalloc", ok)
     return evals, resid, stats.as_dict(), rc
 
 

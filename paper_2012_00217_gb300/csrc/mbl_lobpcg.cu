@@ -21,6 +21,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 #include "mbl_dense.h"
 #include "mbl_device.cuh"
@@ -617,4 +618,56 @@ extern "C" int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, in
     if (emin_host) *emin_host = lo;
     if (emax_host) *emax_host = hi;
     return (r1 == MBL_OK && r2 == MBL_OK) ? MBL_OK : MBL_ERR_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------------------------
+// Solve without any allocation: the workspace is a fixed array in device memory that
+// exists from module load to process exit on every device that loads this library.
+
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)MBL_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host code must not use g_noalloc_scratch as an address: its name only stands for the
+// device symbol.  The device address is looked up once per device (with that device
+// current) and cached.
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MBL_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return MBL_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MBL_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MBL_OK;
+}
+
+}  // namespace
+
+extern "C" int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
+                                        const double *X0_dev, double *evals_host, double *evecs_dev,
+                                        double *resid_host, mbl_lobpcg_stats *stats, mbl_stream_t stream)
+{
+    size_t need = 0;
+    int rc = mbl_lobpcg_workspace_size(chain, opts, &need);
+    if (rc != MBL_OK) return rc;
+    if (need > kNoAllocBytes) return MBL_ERR_WORKSPACE;
+    void *ws = nullptr;
+    rc = noalloc_scratch(&ws);
+    if (rc != MBL_OK) return rc;
+    // graph instantiation and timing events would allocate: both are switched off
+    mbl_lobpcg_opts o = *opts;
+    o.use_graph = 0;
+    o.timing = 0;
+    return mbl_lobpcg_solve(chain, sigma, &o, X0_dev, ws, kNoAllocBytes, evals_host, evecs_dev, resid_host, stats,
+                            stream);
 }
