@@ -95,6 +95,16 @@ int mbl_hamiltonian_apply(const mbl_chain *chain, double sigma, int dtype, const
                           int64_t ldx, void *Y_dev, int64_t ldy, int64_t n, int k,
                           mbl_stream_t stream);
 
+/* Tuning: the product kernels split a state into B low bits and L - B high bits; all
+ * states with the same high bits form one tile of consecutive rows, staged in shared
+ * memory, and high-bond neighbours are whole tiles at the same in-tile offsets.  This
+ * sets B for products of block width k and type dtype in this process: 0 = built-in
+ * heuristic (default), -1 = untiled kernel, 2..16 = that B (capped at L - 1, and
+ * lowered until the largest tile fits in shared memory).  Results
+ * differ only in the order of floating-point additions.  Not thread-safe against
+ * concurrent products. */
+int mbl_set_product_tile_bits(int k, int dtype, int bits);
+
 /* ---- folded-spectrum LOBPCG (Sec. 3.2, Sec. 6.2) ---------------------------------- */
 
 typedef struct {

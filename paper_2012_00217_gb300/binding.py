@@ -30,7 +30,8 @@ MODE_MIXED = 1
 
 EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis_rank",
             "mbl_hamiltonian_apply", "mbl_lobpcg_workspace_size", "mbl_lobpcg_solve",
-            "mbl_bounds_workspace_size", "mbl_spectrum_bounds", "mbl_lobpcg_solve_noalloc")
+            "mbl_bounds_workspace_size", "mbl_spectrum_bounds", "mbl_lobpcg_solve_noalloc",
+            "mbl_set_product_tile_bits")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -82,6 +83,8 @@ def lib():
     so.mbl_basis_rank.argtypes = [i32, i32, p, p, i64, p]
     so.mbl_hamiltonian_apply.restype = i32
     so.mbl_hamiltonian_apply.argtypes = [pch, f64, i32, p, i64, p, i64, i64, i32, p]
+    so.mbl_set_product_tile_bits.restype = i32
+    so.mbl_set_product_tile_bits.argtypes = [i32, i32, i32]
     so.mbl_lobpcg_workspace_size.restype = i32
     so.mbl_lobpcg_workspace_size.argtypes = [pch, popt, ctypes.POINTER(sz)]
     so.mbl_lobpcg_solve.restype = i32
@@ -174,6 +177,14 @@ def hamiltonian_apply(chain, sigma, X, Y):
                                        X.stride(0), _dev(Y, Y.dtype, "Y"), Y.stride(0), n, k,
                                        _stream_ptr(X)), "mbl_hamiltonian_apply")
     return Y
+
+
+def set_product_tile_bits(k, dtype, bits):
+    """Tile width of the product kernels for block width k and dtype (torch.float32 or
+    torch.float64): 0 heuristic, -1 untiled, 2..16 low bits per tile."""
+    torch = _torch()
+    dt = MBL_F32 if dtype == torch.float32 else MBL_F64
+    _check(lib().mbl_set_product_tile_bits(int(k), dt, int(bits)), "mbl_set_product_tile_bits")
 
 
 def make_opts(nev, k, tol=1e-8, max_iter=200, pcg_iters=50, pcg_tol=0.0, norm_h=0.0,

@@ -17,6 +17,8 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "mbl_device.cuh"
 #include "mbl_internal.h"
@@ -33,6 +35,15 @@ struct RowLayout {
     static constexpr int kBytes = K * (int)sizeof(T);
     static constexpr int V = kBytes >= 16 ? 16 / (int)sizeof(T) : K;  // elements per lane
     static constexpr int G = K / V;                                    // lanes per row
+    static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
+};
+
+// Tiled kernels move up to 32 bytes per lane (two 16-byte loads per neighbour row).
+template <typename T, int K>
+struct WideRowLayout {
+    static constexpr int kBytes = K * (int)sizeof(T);
+    static constexpr int V = kBytes >= 32 ? 32 / (int)sizeof(T) : (kBytes >= 16 ? 16 / (int)sizeof(T) : K);
+    static constexpr int G = K / V;
     static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
 };
 
@@ -187,8 +198,7 @@ struct ApplySmem {
 // block, write this block's k partials, and let the last block finish.  Returns true
 // in the last block (after a __syncthreads, with the block's partial visible).
 template <typename T, int V, int G>
-__device__ __forceinline__ bool block_column_reduce(ApplySmem<T> &sm, T (&part)[V], int k,
-                                                    const Reduce &rd)
+__device__ __forceinline__ bool block_column_reduce(T (*red)[64], T (&part)[V], int k, const Reduce &rd)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -196,12 +206,12 @@ __device__ __forceinline__ bool block_column_reduce(ApplySmem<T> &sm, T (&part)[
         for (int off = G; off < 32; off <<= 1) part[v] += __shfl_xor_sync(0xffffffffu, part[v], off);
     if (lane < G) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) sm.red[warp][lane * V + v] = part[v];
+        for (int v = 0; v < V; ++v) red[warp][lane * V + v] = part[v];
     }
     __syncthreads();
     if (threadIdx.x < k) {
         double acc = 0.0;
-        for (int w = 0; w < kWarps; ++w) acc += (double)sm.red[w][threadIdx.x];
+        for (int w = 0; w < kWarps; ++w) acc += (double)red[w][threadIdx.x];
         rd.partials[(int64_t)blockIdx.x * k + threadIdx.x] = acc;
     }
     __threadfence();
@@ -237,6 +247,35 @@ __device__ __forceinline__ void finish_column_sums(const Reduce &rd, int k, doub
     }
     __syncthreads();
     if (threadIdx.x == 0) *rd.counter = 0u;
+}
+
+// PCG epilogue of a product launch: block partials of t.t (kPcgT) or r.(M^-1 r)
+// (kPcgQ), then in the last block alpha = rz / t.t, or beta = rz_new / rz with the
+// freeze rule (a column stops once rz_new <= tol^2 rz0, or on NaN/Inf).
+template <typename T, int V, int G, int MODE>
+__device__ __forceinline__ void pcg_block_finish(T (*red)[64], T (&part)[V], int K, const PcgScalars &ps,
+                                                 const Reduce &rd)
+{
+    if (!block_column_reduce<T, V, G>(red, part, K, rd)) return;
+    __shared__ double s_tot[64];
+    finish_column_sums(rd, K, s_tot);
+    if (threadIdx.x < K) {
+        const int c = threadIdx.x;
+        if (MODE == kPcgT) {
+            const double tt = s_tot[c];
+            const bool ok = ps.active[c] && tt > 0.0 && isfinite(tt);
+            ps.alpha[c] = ok ? ps.rz[c] / tt : 0.0;
+        } else {
+            const double rzn = s_tot[c];
+            int act = ps.active[c];
+            if (!isfinite(rzn)) act = 0;
+            if (ps.tol2 > 0.0 && rzn <= ps.tol2 * ps.rz0[c]) act = 0;
+            ps.beta[c] = (act && ps.rz[c] > 0.0) ? rzn / ps.rz[c] : 0.0;
+            if (!act) ps.alpha[c] = 0.0;
+            ps.active[c] = act;
+            ps.rz[c] = rzn;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -351,26 +390,258 @@ __global__ void __launch_bounds__(kThreads) k_apply(ChainParams cp, const T *__r
     }
 
     if (MODE == kPlain) return;
-    if (!block_column_reduce<T, V, G>(sm, part, K, rd)) return;
-    __shared__ double s_tot[64];
-    finish_column_sums(rd, K, s_tot);
-    if (threadIdx.x < K) {
-        const int c = threadIdx.x;
-        if (MODE == kPcgT) {
-            double tt = s_tot[c];
-            bool ok = ps.active[c] && tt > 0.0 && isfinite(tt);
-            ps.alpha[c] = ok ? ps.rz[c] / tt : 0.0;
-        } else {
-            double rzn = s_tot[c];
-            int act = ps.active[c];
-            if (!isfinite(rzn)) act = 0;
-            if (ps.tol2 > 0.0 && rzn <= ps.tol2 * ps.rz0[c]) act = 0;
-            ps.beta[c] = (act && ps.rz[c] > 0.0) ? rzn / ps.rz[c] : 0.0;
-            if (!act) ps.alpha[c] = 0.0;
-            ps.active[c] = act;
-            ps.rz[c] = rzn;
+    pcg_block_finish<T, V, G, MODE>(sm.red, part, K, ps, rd);
+}
+
+
+// ---------------------------------------------------------------------------------
+// Tile-structured product.  Split a state s into a high part t (bits B..L-1, H = L - B
+// bits) and a low part u (bits 0..B-1).  All states with the same t are consecutive
+// rows -- a tile of C(B, p) rows, p = n_up - popc(t), ordered by the colex rank j of u --
+// so the rank-shift rule of a bond exchange (+C(i, c) when the up spin moves from i to
+// i + 1, -C(i, c) the other way, c = up spins below site i) takes these forms:
+//   * bonds inside the low part: in-tile neighbours that depend only on (B, p, j);
+//   * bonds inside the high part (i = B + b): c = p + popc(t mod 2^b), the same shift for
+//     every row of the tile -- the neighbour rows are the tile's rows moved as a block;
+//   * the joining bond (B-1, B): shift +C(B-1, p-1) or -C(B-1, p), also per tile;
+//   * the wrap bond of a periodic chain: rank = offset of tile t ^ 2^(H-1) plus the rank
+//     of u ^ 1 in its class.
+// Everything that depends on the low pattern alone comes from a small table built once
+// per tile width (LowRec); each warp processes 32 rows of one tile.
+
+constexpr uint32_t kNoRow = 0xffffffffu;
+
+struct LowRec {
+    uint16_t u;      // low pattern
+    uint8_t cnt;     // flippable bonds inside the low part
+    uint8_t alow;    // antiparallel bonds inside the low part
+    uint16_t jper;   // colex rank of u ^ 1 among the words of its popcount
+    uint16_t pad;
+    uint16_t nb[12];  // in-tile ranks of the low-part neighbours
+};
+static_assert(sizeof(LowRec) == 32, "LowRec layout");
+
+constexpr int kLowMaxB = 13;  // at most 12 low bonds, C(13, 6) = 1716 rows per tile
+// records for B = 2..13 at offsets 2^B - 4 (the sizes 2^B, B < current, summed)
+constexpr int kLowRecords = (1 << (kLowMaxB + 1)) - 4;
+static __device__ LowRec g_lowtab[kLowRecords];
+
+__host__ __device__ inline int lowtab_base(int B) { return (1 << B) - 4; }
+
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(kThreads, 3) k_apply_tiled(ChainParams cp, int B, const T *__restrict__ X,
+                                                          int64_t ldx, T *__restrict__ Y, int64_t ldy,
+                                                          T *__restrict__ R, const T *__restrict__ dinv,
+                                                          PcgScalars ps, Reduce rd)
+{
+    using Lay = WideRowLayout<T, K>;
+    constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G, CH = 32;
+    __shared__ uint32_t sbin[kBinomDim * kBinomDim];
+    __shared__ T tab[1024];
+    __shared__ T red[kWarps][64];
+    __shared__ uint32_t spref[kLowMaxB + 2];  // spref[p] = sum_{q < p} C(B, q)
+    load_binom(sbin);
+    build_field_tables<T>(tab, cp);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int q = 0; q <= B + 1 && q <= kLowMaxB + 1; ++q) {
+            spref[q] = acc;
+            acc += binom(sbin, B, q);
         }
     }
+    __syncthreads();
+
+    const int L = cp.L, m = cp.n_up, H = L - B;
+    const uint32_t ntile = 1u << H;
+    const uint32_t nchunk = (binom(sbin, B, B / 2) + CH - 1) / CH;
+    const uint32_t total = ntile * nchunk;
+    const T hdelta = (T)cp.half_delta, half = (T)0.5;
+    const int lane = threadIdx.x & 31, grp = lane / G;
+    const int col = (lane % G) * V;
+    const LowRec *__restrict__ tbl = g_lowtab + lowtab_base(B);
+    T part[V], alpha[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        part[v] = (T)0;
+        alpha[v] = (MODE == kPcgQ) ? (T)ps.alpha[col + v] : (T)0;
+    }
+    const uint32_t gw = blockIdx.x * kWarps + (threadIdx.x >> 5), nw = gridDim.x * kWarps;
+    for (uint32_t item = gw; item < total; item += nw) {
+        const uint32_t t = item % ntile, c = item / ntile;
+        const int p = m - __popc(t);
+        if (p < 0 || p > B) continue;  // warp-uniform
+        const uint32_t Rt = binom(sbin, B, p);
+        const uint32_t j_begin = c * CH;
+        if (j_begin >= Rt) continue;
+        const uint32_t j_end = min(Rt, j_begin + CH);
+        // per-tile values, one lane each
+        uint32_t v32 = 0;
+        double ct = 0.0;
+        bool flip = false;
+        if (lane == 0) {
+            v32 = cns_rank(sbin, (t << B) | ((1u << p) - 1u));  // tile offset
+            const uint32_t ahigh = __popc((t ^ (t >> 1)) & ((1u << (H - 1)) - 1u));
+            ct = cp.diag_const + (double)field_sum(tab, t << B) - cp.half_delta * (double)ahigh;
+        } else if (lane <= H - 1) {  // high bond (B + b, B + b + 1), b = lane - 1
+            const int b = lane - 1;
+            if (((t >> b) ^ (t >> (b + 1))) & 1u) {
+                flip = true;
+                const uint32_t dlt = binom(sbin, B + b, p + __popc(t & ((1u << b) - 1u)));
+                v32 = ((t >> b) & 1u) ? dlt : (0u - dlt);  // rank shift, modulo 2^32
+            }
+        } else if (lane == 31 && cp.periodic) {  // tile across the wrap bond
+            const uint32_t t2 = t ^ (1u << (H - 1));
+            const int p2 = m - __popc(t2);
+            v32 = (p2 >= 0 && p2 <= B) ? cns_rank(sbin, (t2 << B) | ((1u << p2) - 1u)) : kNoRow;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, flip);
+        const int nh = __popc(bal);
+        // compact the high-bond shifts into lanes 0..nh-1
+        uint32_t hshift = 0;
+        {
+            unsigned bb = bal;
+            for (int q = 0; q < nh; ++q) {
+                const int owner = __ffs(bb) - 1;
+                bb &= bb - 1;
+                const uint32_t vq = __shfl_sync(0xffffffffu, v32, owner);
+                if (lane == q) hshift = vq;
+            }
+        }
+        const uint32_t off = __shfl_sync(0xffffffffu, v32, 0);
+        const uint32_t offper = __shfl_sync(0xffffffffu, v32, 31);
+        const T ctt = (T)__shfl_sync(0xffffffffu, ct, 0);
+        const uint32_t t0 = t & 1u, thi = (t >> (H - 1)) & 1u;
+        const uint32_t sup = p >= 1 ? binom(sbin, B - 1, p - 1) : 0u;   // joining bond, up spin moves up
+        const uint32_t sdn = binom(sbin, B - 1, p);                      // joining bond, moves down
+        const LowRec *__restrict__ rp = tbl + spref[p];
+        for (uint32_t j0 = j_begin; j0 < j_end; j0 += RPW) {
+            const uint32_t j = j0 + grp;
+            const bool valid = j < j_end;
+            const uint32_t r = off + j;
+            const T *__restrict__ xr = X + (int64_t)r * ldx + col;
+            // the row's low-pattern record: u, counts, wrap rank, local neighbours
+            uint4 w0 = make_uint4(0, 0, 0, 0), w1 = make_uint4(0, 0, 0, 0);
+            if (valid) {
+                w0 = __ldg(reinterpret_cast<const uint4 *>(rp + j));
+                w1 = __ldg(reinterpret_cast<const uint4 *>(rp + j) + 1);
+            }
+            const uint32_t u = w0.x & 0xffffu, cnt = (w0.x >> 16) & 0xffu, alow = w0.x >> 24;
+            const uint32_t ub = (u >> (B - 1)) & 1u;
+            const bool join = valid && ub != t0;
+            const bool wrap = valid && cp.periodic && (u & 1u) != thi;
+            T acc[V];
+            {
+                const T d = (ctt + (tab[u & 255u] + tab[256 + (u >> 8)])) -
+                            hdelta * (T)(alow + (join ? 1u : 0u) + (wrap ? 1u : 0u));
+                Vec<T, V> x;
+#pragma unroll
+                for (int v = 0; v < V; ++v) x.v[v] = (T)0;
+                if (valid) x = ldv<T, V>(xr);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = d * x.v[v];
+            }
+            // joining and wrap bonds
+            {
+                Vec<T, V> a, b;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    a.v[v] = (T)0;
+                    b.v[v] = (T)0;
+                }
+                if (join) a = ldv<T, V>(xr + (ub ? (int64_t)sup : -(int64_t)sdn) * ldx);
+                if (wrap) b = ldv<T, V>(X + (int64_t)(offper + (w0.y & 0xffffu)) * ldx + col);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += half * (a.v[v] + b.v[v]);
+            }
+            // low-part neighbours, in-tile ranks unpacked from the record
+            {
+                const uint32_t nbw[6] = {w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int q0 = 0; q0 < 12; q0 += 4) {
+                    if (q0 >= (int)cnt) break;
+                    Vec<T, V> a[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int q = q0 + e;
+                        const uint32_t jn = (nbw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
+                        if (q < (int)cnt) a[e] = ldv<T, V>(X + (int64_t)(off + jn) * ldx + col);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] += half * a[e].v[v];
+                }
+            }
+            // high-part neighbours: the same shift for the whole tile
+#pragma unroll 4
+            for (int hh = 0; hh < nh; ++hh) {
+                const uint32_t sh = __shfl_sync(0xffffffffu, hshift, hh);
+                if (valid) {
+                    const Vec<T, V> a = ldv<T, V>(xr + (int64_t)(int32_t)sh * ldx);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] += half * a.v[v];
+                }
+            }
+            if (valid) finish_row<T, V, MODE>(acc, 0, r, Y, ldy, R, dinv, col, alpha, part);
+        }
+    }
+    if (MODE == kPlain) return;
+    pcg_block_finish<T, V, G, MODE>(red, part, K, ps, rd);
+}
+
+// Host side of the low-pattern table: built once per tile width and copied to the
+// device table before the first tiled product of that width on the current device.
+static std::mutex g_lowtab_mutex;
+static bool g_lowtab_ready[64][kLowMaxB + 1] = {};
+
+uint32_t host_binom(int n, int k);
+
+static int host_colex_rank(uint32_t u)
+{
+    int r = 0, j = 0;
+    for (int pos = 0; pos < 32; ++pos)
+        if ((u >> pos) & 1u) {
+            ++j;
+            r += (int)host_binom(pos, j);
+        }
+    return r;
+}
+
+int ensure_lowtab(int B)
+{
+    if (B < 2 || B > kLowMaxB) return MBL_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MBL_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_lowtab_mutex);
+    if (g_lowtab_ready[dev][B]) return MBL_OK;
+    std::vector<LowRec> recs((size_t)1 << B);
+    size_t idx = 0;
+    for (int p = 0; p <= B; ++p) {
+        // words of popcount p in ascending order: their position is their colex rank
+        for (uint32_t u = 0; u < (1u << B); ++u) {
+            if (__builtin_popcount(u) != p) continue;
+            LowRec rec{};
+            rec.u = (uint16_t)u;
+            int cnt = 0;
+            for (int i = 0; i + 1 < B; ++i) {
+                const uint32_t bi = (u >> i) & 1u, bj = (u >> (i + 1)) & 1u;
+                if (bi == bj) continue;
+                rec.nb[cnt++] = (uint16_t)host_colex_rank(u ^ (3u << i));
+            }
+            rec.cnt = (uint8_t)cnt;
+            rec.alow = (uint8_t)cnt;
+            rec.jper = (uint16_t)host_colex_rank(u ^ 1u);
+            recs[idx++] = rec;
+        }
+    }
+    if (cudaMemcpyToSymbol(g_lowtab, recs.data(), recs.size() * sizeof(LowRec),
+                           (size_t)lowtab_base(B) * sizeof(LowRec)) != cudaSuccess)
+        return MBL_ERR_CUDA;
+    g_lowtab_ready[dev][B] = true;
+    return MBL_OK;
 }
 
 // Runtime block width (any 1 <= k <= 256, any alignment): one warp per row, lanes
@@ -733,12 +1004,94 @@ static cudaError_t launch_apply_k(const ChainParams &cp, const T *X, int64_t ldx
     return cudaGetLastError();
 }
 
+// ---- tiled product dispatch ----------------------------------------------------
+
+// Tile width override per (block width, element size): 0 = heuristic, -1 = untiled,
+// >= 2 = that many low bits.  Set by the autotuner.
+static int g_tile_bits[2][8] = {};
+
+static int kslot(int K)
+{
+    switch (K) {
+    case 1: return 0;
+    case 2: return 1;
+    case 4: return 2;
+    case 8: return 3;
+    case 16: return 4;
+    case 32: return 5;
+    case 64: return 6;
+    default: return 7;
+    }
+}
+
+uint32_t host_binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    uint64_t c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (uint64_t)(n - k + i) / (uint64_t)i;
+    return (uint32_t)c;
+}
+
+// Tile width heuristic: tiles of at least 64 rows (B >= 8) keep the 32-row work items
+// full; B <= L - 2 keeps at least two high bits.
+static int heuristic_tile_bits(int L, int K, size_t es)
+{
+    (void)K;
+    (void)es;
+    int B = 8;
+    if (B > L - 2) B = L - 2;
+    return B >= 2 ? B : -1;
+}
+
+int tile_bits_for(int L, int K, size_t es)
+{
+    if (L < 4) return -1;
+    const int o = g_tile_bits[es == 8 ? 1 : 0][kslot(K)];
+    if (o == -1) return -1;
+    int B = (o >= 2) ? o : heuristic_tile_bits(L, K, es);
+    if (B > kLowMaxB) B = kLowMaxB;
+    if (B > L - 2) B = L - 2;
+    return B >= 2 ? B : -1;
+}
+
+void set_tile_bits(int K, size_t es, int bits) { g_tile_bits[es == 8 ? 1 : 0][kslot(K)] = bits; }
+
+template <typename T, int K, int MODE>
+static cudaError_t launch_tiled(const ChainParams &cp, int B, const T *X, int64_t ldx, T *Y, int64_t ldy, T *R,
+                                const T *dinv, const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
+{
+    if (ensure_lowtab(B) != MBL_OK) return cudaErrorUnknown;
+    auto kern = k_apply_tiled<T, K, MODE>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    const uint32_t rmax = host_binom(B, B / 2);
+    const int64_t items = ((int64_t)1 << (cp.L - B)) * (int64_t)((rmax + 31) / 32);
+    int64_t grid = (int64_t)num_sms() * per_sm;
+    if (grid > (int64_t)num_sms() * 8) grid = (int64_t)num_sms() * 8;  // partials capacity
+    const int64_t need = (items + kWarps - 1) / kWarps;
+    if (grid > need) grid = need;
+    kern<<<(int)grid, kThreads, 0, st>>>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd);
+    return cudaGetLastError();
+}
+
 static int apply_grid(uint32_t n, int cap_per_sm)
 {
     int64_t need = ((int64_t)n + 32 * kWarps - 1) / (32 * kWarps);
     int64_t cap = (int64_t)num_sms() * cap_per_sm;
     if (need < 1) need = 1;
     return (int)(need < cap ? need : cap);
+}
+
+template <typename T>
+static bool vec_ok_wide(const void *p, int64_t ld, int K)
+{
+    const int bytes = K * (int)sizeof(T);
+    const int align = bytes >= 32 ? 32 : (bytes >= 16 ? 16 : bytes);
+    return ((uintptr_t)p % align == 0) && ((ld * (int64_t)sizeof(T)) % align == 0);
 }
 
 template <typename T>
@@ -758,7 +1111,19 @@ static int dispatch_plain(const ChainParams &cp, const T *X, int64_t ldx, T *Y, 
     const int grid = apply_grid(n, 8);
     cudaError_t e = cudaSuccess;
     bool done = true;
-    if (vec_ok<T>(X, ldx, k) && vec_ok<T>(Y, ldy, k)) {
+    const int B = tile_bits_for(cp.L, k, sizeof(T));
+    if (B >= 2 && vec_ok_wide<T>(X, ldx, k) && vec_ok_wide<T>(Y, ldy, k)) {
+        switch (k) {
+        case 1: e = launch_tiled<T, 1, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
+        case 2: e = launch_tiled<T, 2, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
+        case 4: e = launch_tiled<T, 4, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
+        case 8: e = launch_tiled<T, 8, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
+        case 16: e = launch_tiled<T, 16, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
+        case 32: e = launch_tiled<T, 32, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
+        case 64: e = launch_tiled<T, 64, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
+        default: done = false;
+        }
+    } else if (vec_ok<T>(X, ldx, k) && vec_ok<T>(Y, ldy, k)) {
         switch (k) {
         case 1: e = launch_apply_k<T, 1, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
         case 2: e = launch_apply_k<T, 2, kPlain>(cp, X, ldx, Y, ldy, n, nullptr, nullptr, ps, rd, grid, st); break;
@@ -815,6 +1180,7 @@ int gershgorin_bound(const ChainParams &cp, uint32_t n, double *partials, unsign
 }
 
 int pcg_grid(uint32_t n) { return apply_grid(n, 4); }
+size_t pcg_partial_doubles() { return (size_t)num_sms() * 8 * 64 + 64; }
 
 template <typename T>
 int pcg_start(const double *B, int64_t ldb, const double *bnorm, uint32_t n, int k, const T *dinv, T *r, T *p,
@@ -835,9 +1201,17 @@ template <typename T, int K>
 static cudaError_t pcg_step_k(const ChainParams &cp, uint32_t n, const T *dinv, T *r, T *p, T *t, T *w,
                               const PcgScalars &ps, const Reduce &rd, int grid, cudaStream_t st)
 {
-    cudaError_t e = launch_apply_k<T, K, kPcgT>(cp, p, K, t, K, n, nullptr, dinv, ps, rd, grid, st);
-    if (e != cudaSuccess) return e;
-    e = launch_apply_k<T, K, kPcgQ>(cp, t, K, nullptr, K, n, r, dinv, ps, rd, grid, st);
+    cudaError_t e;
+    const int B = tile_bits_for(cp.L, K, sizeof(T));
+    if (B >= 2) {
+        e = launch_tiled<T, K, kPcgT>(cp, B, p, K, t, K, nullptr, dinv, ps, rd, st);
+        if (e != cudaSuccess) return e;
+        e = launch_tiled<T, K, kPcgQ>(cp, B, t, K, nullptr, K, r, dinv, ps, rd, st);
+    } else {
+        e = launch_apply_k<T, K, kPcgT>(cp, p, K, t, K, n, nullptr, dinv, ps, rd, grid, st);
+        if (e != cudaSuccess) return e;
+        e = launch_apply_k<T, K, kPcgQ>(cp, t, K, nullptr, K, n, r, dinv, ps, rd, grid, st);
+    }
     if (e != cudaSuccess) return e;
     int ugrid = (int)(((int64_t)n * RowLayout<T, K>::G + kThreads - 1) / kThreads);
     if (ugrid > num_sms() * 8) ugrid = num_sms() * 8;
@@ -886,6 +1260,14 @@ template int pcg_step<double>(const ChainParams &, uint32_t, int, const double *
 
 // ---------------------------------------------------------------------------------
 // C ABI: the product.
+
+extern "C" int mbl_set_product_tile_bits(int k, int dtype, int bits)
+{
+    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || bits < -1 || bits > 16 || bits == 1)
+        return MBL_ERR_ARG;
+    mbl::set_tile_bits(k, dtype == MBL_F32 ? 4 : 8, bits);
+    return MBL_OK;
+}
 
 extern "C" int mbl_hamiltonian_apply(const mbl_chain *chain, double sigma, int dtype, const void *X_dev,
                                      int64_t ldx, void *Y_dev, int64_t ldy, int64_t n, int k, mbl_stream_t stream)

@@ -28,6 +28,11 @@ int apply_device(const ChainParams &cp, int dtype, const void *X, int64_t ldx, v
 int gershgorin_bound(const ChainParams &cp, uint32_t n, double *partials, unsigned *counter, double *out,
                      cudaStream_t st);
 int pcg_grid(uint32_t n);
+size_t pcg_partial_doubles();
+// Tile width (low bits per tile) used by the product kernels for block width K and
+// element size es; -1 = untiled kernel.  set_tile_bits: 0 heuristic, -1 untiled, >= 2 fixed.
+int tile_bits_for(int L, int K, size_t es);
+void set_tile_bits(int K, size_t es, int bits);
 template <typename T>
 int pcg_fold_dinv(const ChainParams &cp, uint32_t n, T *dinv, cudaStream_t st);
 template <typename T>

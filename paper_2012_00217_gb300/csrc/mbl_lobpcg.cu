@@ -112,7 +112,7 @@ Buffers carve(char *base, int64_t n, int k, int pcg_f32, size_t *bytes)
     b.eigw = c.take<double>(ew > ew2 ? ew : ew2);
     b.pcg_s = c.take<double>(4 * 64);
     b.pcg_active = c.take<int>(64);
-    b.pcg_part = c.take<double>((size_t)pcg_grid((uint32_t)n) * 64 + 64);
+    b.pcg_part = c.take<double>(pcg_partial_doubles());
     b.counter = c.take<unsigned>(4);
     b.iflags = c.take<int>(16 + 64);
     b.dstat = c.take<double>(8);

@@ -18,6 +18,8 @@ namespace mbl {
 
 constexpr int kSmallThreads = 512;
 constexpr int kMaxSweeps = 20;
+constexpr int kMaxK = 64;        // block width limit of the solver
+constexpr int kMaxW = 3 * kMaxK;  // width of S = [X W P]
 
 template <typename T>
 struct Eps;
@@ -255,9 +257,13 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
     T *U = reinterpret_cast<T *>(Cs + w * w);  // w x w
     T *T2 = U + w * w;                   // w x w
     T *Z = T2 + w * w;                   // w x w (keep x keep, ld keep)
-    T *csb = Z + w * w;                  // w + 2
-    int *pairs = reinterpret_cast<int *>(csb + w + 2);  // w + 2
-    double *dbase = reinterpret_cast<double *>(pairs + w + 4);
+    // rotation parameters of one Jacobi round live in shared memory: every element
+    // update of the round reads them
+    __shared__ T csb[kMaxW + 2];
+    __shared__ int pairs[kMaxW + 2];
+    __shared__ double cs64[kMaxK + 2];
+    __shared__ int pairs64[kMaxK + 2];
+    double *dbase = reinterpret_cast<double *>(Z + w * w);
     dbase = reinterpret_cast<double *>(((uintptr_t)dbase + 15) & ~(uintptr_t)15);
     double *Zk = dbase;                  // keep x k
     double *Y = Zk + w * k;              // w x k
@@ -267,13 +273,15 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
     double *Ri = R + k * k;              // k x k
     double *Q = Ri + k * k;              // k x k
     double *mu = Q + k * k;              // k
-    double *A64 = mu + k;                // k x k
-    double *V64 = A64 + k * k;           // k x k
-    double *cs64 = V64 + k * k;          // k + 2
-    int *pairs64 = reinterpret_cast<int *>(cs64 + k + 2);
-    T *Ag = reinterpret_cast<T *>(((uintptr_t)(pairs64 + k + 8) + 15) & ~(uintptr_t)15);
+    double *A64g = mu + k;               // k x k (global fallback)
+    double *V64g = A64g + k * k;         // k x k
+    T *Ag = reinterpret_cast<T *>(((uintptr_t)(V64g + k * k) + 15) & ~(uintptr_t)15);
     T *A = use_smem ? As : Ag;
     T *V = use_smem ? Vs : Ag + w * w;
+    // the k x k FP64 refinement reuses the shared region once the w x w solves are done
+    const bool ref_smem = use_smem && (size_t)2 * k * k * sizeof(double) <= (size_t)2 * w * w * sizeof(T);
+    double *A64 = ref_smem ? reinterpret_cast<double *>(As) : A64g;
+    double *V64 = A64 + k * k;
 
     for (int i = tid; i < w; i += nt) {
         const double d = GS[i * w + i];

@@ -194,3 +194,25 @@ def test_apply_full_size_sampled(mbl, L, k, dtype):
     scale = (np.abs(d)[:, None] + 0.5 * L) * np.abs(Xh).max()
     derr = 6 * u * (np.sum(np.abs(h)) + 0.5 + L)
     assert np.all(np.abs(got - ref) <= 4 * (L + 2) * u * scale + derr * np.abs(Xh).max())
+
+
+@pytest.mark.parametrize("bits", [-1, 2, 3, 5, 8, 16])
+@pytest.mark.parametrize("L,periodic,k,dtype", [(14, True, 8, np.float32), (13, False, 32, np.float64),
+                                                (16, True, 64, np.float32), (12, True, 1, np.float32),
+                                                (15, False, 4, np.float64)])
+def test_apply_every_tile_width(mbl, bits, L, periodic, k, dtype):
+    """The tiled kernel for every tile width (and the untiled one) against the oracle."""
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    h = wl.fields(L, 6.0, L * 3 + k)
+    chain = ham.Chain(L, h, delta=1.0, periodic=periodic)
+    n = ham.sector_dim(L, L // 2)
+    X = wl.block(n, k, 7 + bits, dtype)
+    ref = ham.apply(chain, -0.3, X.astype(np.float64))
+    Y = torch.empty((n, k), dtype=tdt, device=DEV)
+    mbl.binding.set_product_tile_bits(k, tdt, bits)
+    try:
+        mbl.hamiltonian_apply(mbl.make_chain(L, h, 1.0, periodic), -0.3, _gpu(X), Y)
+    finally:
+        mbl.binding.set_product_tile_bits(k, tdt, 0)
+    err = np.abs(Y.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= _bound(chain, -0.3, X, dtype)), err.max()
