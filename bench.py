@@ -287,7 +287,8 @@ def run_reference(args):
 
 def run_profile(args):
     """Small fixed workloads for ncu: 'product' launches the L = 20 (k = 32) and L = 26
-    (k = 64) FP32 block products three times each; 'pcg' runs a 3-iteration solve."""
+    (k = 64) FP32 block products three times each; 'pcg' runs a 3-iteration solve;
+    'bounds' runs the spectrum bounds of the bench workload once."""
     import torch
     import paper_2012_00217_gb300 as mbl
     dev = torch.device("cuda:0")
@@ -305,6 +306,11 @@ def run_profile(args):
                 mbl.hamiltonian_apply(chain, 0.0, X, Y)
             torch.cuda.synchronize()
             del X, Y
+    elif args.profile == "bounds":
+        s = _setup(torch, mbl, dev)
+        step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
+        mbl.spectrum_bounds(s["chain"], step.Xb, step.ws, tol=BOUNDS_TOL, max_iter=1000)
+        torch.cuda.synchronize()
     else:
         s = _setup(torch, mbl, dev)
         step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
@@ -326,7 +332,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the sweep and the CPU baseline")
-    ap.add_argument("--profile", choices=["product", "pcg"], default=None,
+    ap.add_argument("--profile", choices=["product", "pcg", "bounds"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
                          "FP32) or a 3-iteration solve, for an ncu capture")
     args = ap.parse_args()
@@ -380,6 +386,9 @@ def main():
     step64.run()
     t64 = _time_steps(torch, step64.run, 1, flush)[0]
     res64 = step64.last
+    # spectrum bounds alone (the first part of every step)
+    t_b = _time_steps(torch, lambda: mbl.spectrum_bounds(s["chain"], step.Xb, step.ws, tol=BOUNDS_TOL,
+                                                         max_iter=1000), 1, flush)[0]
     # per-phase device time of one solve (events between phases; graphs off)
     step.opts.timing = 1
     step.run()
@@ -420,6 +429,7 @@ def main():
         "roofline": None,
         "solve_kernel": kern,
         "solve_phases_s": phases,
+        "bounds_s": t_b,
         "matvec_sweep": sweep,
         "clocks": ck,
     }

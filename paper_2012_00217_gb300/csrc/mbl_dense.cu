@@ -16,58 +16,63 @@
 namespace mbl {
 
 // ---------------------------------------------------------------------------------
-// Gram: partial tiles.  Block (tp, tq, slab) computes the 64 x 64 output tile
-// (tp, tq) over rows [slab * rows_per_slab, ...).  256 threads, 4 x 4 outputs each.
-constexpr int kGT = 64;   // output tile
-constexpr int kGR = 16;   // rows staged per step
+// Gram: partial tiles.  Block (tp, tq, slab) computes the TS x TS output tile (tp, tq)
+// over rows [slab * rows_per_slab, ...).  256 threads (16 x 16), MT x MT outputs each
+// (MT = TS / 16); threads whose outputs all lie outside p x q only help with staging, so
+// small Grams cost what they compute.
+constexpr int kGR = 16;  // rows staged per step
 
-template <typename CT>
+template <typename CT, int TS>
 __global__ void __launch_bounds__(256) k_gram_partial(const double *__restrict__ A, int64_t lda, int p,
                                                       const double *__restrict__ B, int64_t ldb, int q,
                                                       int64_t n, int64_t rows_per_slab, double *__restrict__ part)
 {
-    __shared__ CT As[kGR][kGT + 1];
-    __shared__ CT Bs[kGR][kGT + 1];
+    constexpr int MT = TS / 16;
+    __shared__ CT As[kGR][TS + 1];
+    __shared__ CT Bs[kGR][TS + 1];
     const int tp = blockIdx.x, tq = blockIdx.y, slab = blockIdx.z;
-    const int p0 = tp * kGT, q0 = tq * kGT;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
-    CT acc[4][4];
+    const int p0 = tp * TS, q0 = tq * TS;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const bool active = (p0 + ty < p) && (q0 + tx < q);
+    CT acc[MT][MT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = (CT)0;
+        for (int j = 0; j < MT; ++j) acc[i][j] = (CT)0;
     const int64_t r_begin = (int64_t)slab * rows_per_slab;
     int64_t r_end = r_begin + rows_per_slab;
     if (r_end > n) r_end = n;
+    const int pw = min(TS, p - p0), qw = min(TS, q - q0);
     for (int64_t r0 = r_begin; r0 < r_end; r0 += kGR) {
-        // stage kGR rows x 64 columns of A and B (coalesced along columns)
-        for (int e = threadIdx.x; e < kGR * kGT; e += 256) {
-            const int rr = e / kGT, cc = e % kGT;
+        for (int e = threadIdx.x; e < kGR * TS; e += 256) {
+            const int rr = e / TS, cc = e % TS;
             const int64_t row = r0 + rr;
             const bool in = row < r_end;
-            As[rr][cc] = (in && p0 + cc < p) ? (CT)A[row * lda + p0 + cc] : (CT)0;
-            Bs[rr][cc] = (in && q0 + cc < q) ? (CT)B[row * ldb + q0 + cc] : (CT)0;
+            As[rr][cc] = (in && cc < pw) ? (CT)A[row * lda + p0 + cc] : (CT)0;
+            Bs[rr][cc] = (in && cc < qw) ? (CT)B[row * ldb + q0 + cc] : (CT)0;
         }
         __syncthreads();
+        if (active) {
 #pragma unroll 4
-        for (int rr = 0; rr < kGR; ++rr) {
-            CT a[4], b[4];
+            for (int rr = 0; rr < kGR; ++rr) {
+                CT a[MT], b[MT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[rr][ty + 16 * i];
+                for (int i = 0; i < MT; ++i) a[i] = As[rr][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[rr][tx + 16 * j];
+                for (int j = 0; j < MT; ++j) b[j] = Bs[rr][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < MT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+                    for (int j = 0; j < MT; ++j) acc[i][j] += a[i] * b[j];
+            }
         }
         __syncthreads();
     }
     double *out = part + (int64_t)slab * p * q;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < MT; ++j) {
             const int pi = p0 + ty + 16 * i, qj = q0 + tx + 16 * j;
             if (pi < p && qj < q) out[(int64_t)pi * q + qj] = (double)acc[i][j];
         }
@@ -90,9 +95,18 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ 
     C[(int64_t)i * ldc + j] = s;
 }
 
+// Output tile edge: 64 when both sizes are multiples of 64, 16 for tiny outputs, else 32.
+static int gram_tile(int p, int q)
+{
+    if (p % 64 == 0 && q % 64 == 0) return 64;
+    if (p <= 16 && q <= 16) return 16;
+    return 32;
+}
+
 static int gram_slabs(int64_t n, int p, int q)
 {
-    const int tiles = ((p + kGT - 1) / kGT) * ((q + kGT - 1) / kGT);
+    const int ts = gram_tile(p, q);
+    const int tiles = ((p + ts - 1) / ts) * ((q + ts - 1) / ts);
     int want = (2 * num_sms() + tiles - 1) / tiles;
     int64_t max_by_rows = (n + 255) / 256;  // at least 256 rows per slab
     if (want > max_by_rows) want = (int)max_by_rows;
@@ -102,16 +116,29 @@ static int gram_slabs(int64_t n, int p, int q)
 
 size_t gram_partial_doubles(int64_t n, int p, int q) { return (size_t)gram_slabs(n, p, q) * p * q; }
 
+template <typename CT, int TS>
+static void launch_gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n,
+                        int64_t rps, int nslab, double *part, cudaStream_t st)
+{
+    dim3 grid((p + TS - 1) / TS, (q + TS - 1) / TS, nslab);
+    k_gram_partial<CT, TS><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rps, part);
+}
+
 int gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n, double *C,
          int64_t ldc, int sym, int compute_f32, double *part, cudaStream_t st)
 {
     const int nslab = gram_slabs(n, p, q);
     const int64_t rps = (n + nslab - 1) / nslab;
-    dim3 grid((p + kGT - 1) / kGT, (q + kGT - 1) / kGT, nslab);
-    if (compute_f32)
-        k_gram_partial<float><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rps, part);
-    else
-        k_gram_partial<double><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rps, part);
+    const int ts = gram_tile(p, q);
+    if (compute_f32) {
+        if (ts == 64) launch_gram<float, 64>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
+        else if (ts == 32) launch_gram<float, 32>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
+        else launch_gram<float, 16>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
+    } else {
+        if (ts == 64) launch_gram<double, 64>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
+        else if (ts == 32) launch_gram<double, 32>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
+        else launch_gram<double, 16>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
+    }
     k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }

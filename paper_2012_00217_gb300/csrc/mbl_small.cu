@@ -32,19 +32,24 @@ struct Eps<double> {
     static __device__ __forceinline__ double v() { return 2.3e-16; }
 };
 
-// Parallel cyclic Jacobi on the symmetric n x n matrix A (row-major, ld n): the
-// round-robin (circle) ordering rotates n/2 disjoint pairs per round.  A rotation
-// zeroes a_pq with t = sign(tau)/(|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp)/(2 a_pq);
-// pairs with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped (the relative test keeps the
-// small eigenvalues of graded matrices accurate), and the sweeps stop when a sweep
-// rotates nothing or after max_sweeps.  On exit diag(A) holds the
-// eigenvalues and the columns of V the eigenvectors.  cs: n + 2 values, pairs: n + 2
-// ints (shared or global).
+// Odd row stride for matrices in shared memory: walking down a column then touches a
+// different bank in every lane.
+__host__ __device__ inline int pad_ld(int n) { return n | 1; }
+
+// Parallel cyclic Jacobi on the symmetric n x n matrix A (row stride ld): the
+// round-robin (circle) ordering rotates n/2 disjoint pairs per round.  A rotation zeroes
+// a_pq with t = sign(tau)/(|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp)/(2 a_pq); pairs
+// with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped (the relative test keeps the small
+// eigenvalues of graded matrices accurate); sweeps stop when one rotates nothing or after
+// max_sweeps.  On exit diag(A) holds the eigenvalues and the columns of V (stride ld)
+// the eigenvectors.  Each warp rotates whole rows / columns of its pairs, lanes striding
+// the other index.  cs, pairs: n + 2 entries (shared memory).
 template <typename T>
-__device__ void dev_jacobi(int n, T *A, T *V, T *cs, int *pairs, int *s_rot, int max_sweeps)
+__device__ void dev_jacobi(int n, int ld, T *A, T *V, T *cs, int *pairs, int *s_rot, int max_sweeps)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < n * n; e += nt) V[e] = (e / n == e % n) ? (T)1 : (T)0;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    for (int i = warp; i < n; i += nwarps)
+        for (int j = lane; j < n; j += 32) V[i * ld + j] = (i == j) ? (T)1 : (T)0;
     __syncthreads();
     if (n < 2) return;
     const int np = (n + 1) & ~1;
@@ -70,7 +75,7 @@ __device__ void dev_jacobi(int n, T *A, T *V, T *cs, int *pairs, int *s_rot, int
                 }
                 T c = (T)1, s = (T)0;
                 if (q < n) {
-                    const T apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
+                    const T apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
                     if (apq != (T)0 && fabs(apq) > eps * sqrt(fabs(app * aqq))) {
                         const T tau = (aqq - app) / ((T)2 * apq);
                         const T t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
@@ -85,29 +90,32 @@ __device__ void dev_jacobi(int n, T *A, T *V, T *cs, int *pairs, int *s_rot, int
                 cs[2 * i + 1] = s;
             }
             __syncthreads();
-            for (int e = tid; e < half * n; e += nt) {
-                const int i = e / n, j = e % n;
+            for (int i = warp; i < half; i += nwarps) {  // rows p, q
                 const T s = cs[2 * i + 1];
                 if (s == (T)0) continue;
-                const int p = pairs[2 * i], q = pairs[2 * i + 1];
                 const T c = cs[2 * i];
-                const T ap = A[p * n + j], aq = A[q * n + j];
-                A[p * n + j] = c * ap - s * aq;
-                A[q * n + j] = s * ap + c * aq;
+                T *Ap = A + pairs[2 * i] * ld, *Aq = A + pairs[2 * i + 1] * ld;
+                for (int j = lane; j < n; j += 32) {
+                    const T ap = Ap[j], aq = Aq[j];
+                    Ap[j] = c * ap - s * aq;
+                    Aq[j] = s * ap + c * aq;
+                }
             }
             __syncthreads();
-            for (int e = tid; e < half * n; e += nt) {
-                const int i = e / n, j = e % n;
+            for (int i = warp; i < half; i += nwarps) {  // columns p, q of A and V
                 const T s = cs[2 * i + 1];
                 if (s == (T)0) continue;
-                const int p = pairs[2 * i], q = pairs[2 * i + 1];
                 const T c = cs[2 * i];
-                const T ap = A[j * n + p], aq = A[j * n + q];
-                A[j * n + p] = c * ap - s * aq;
-                A[j * n + q] = s * ap + c * aq;
-                const T vp = V[j * n + p], vq = V[j * n + q];
-                V[j * n + p] = c * vp - s * vq;
-                V[j * n + q] = s * vp + c * vq;
+                const int p = pairs[2 * i], q = pairs[2 * i + 1];
+                for (int j = lane; j < n; j += 32) {
+                    T *Aj = A + j * ld, *Vj = V + j * ld;
+                    const T ap = Aj[p], aq = Aj[q];
+                    Aj[p] = c * ap - s * aq;
+                    Aj[q] = s * ap + c * aq;
+                    const T vp = Vj[p], vq = Vj[q];
+                    Vj[p] = c * vp - s * vq;
+                    Vj[q] = s * vp + c * vq;
+                }
             }
             __syncthreads();
         }
@@ -118,20 +126,20 @@ __device__ void dev_jacobi(int n, T *A, T *V, T *cs, int *pairs, int *s_rot, int
 }
 
 // Ascending sort of the eigenpairs left by dev_jacobi: w[rank] = A[j][j],
-// Vs[:, rank] = V[:, j] (Vs ld n).
+// Vs[:, rank] = V[:, j] (Vs row stride ldo).
 template <typename T, typename TO>
-__device__ void dev_sort_eig(int n, const T *A, const T *V, TO *w, TO *Vs)
+__device__ void dev_sort_eig(int n, int ld, const T *A, const T *V, TO *w, TO *Vs, int ldo)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int j = tid; j < n; j += nt) {
-        const T lj = A[j * n + j];
+        const T lj = A[j * ld + j];
         int rank = 0;
         for (int i = 0; i < n; ++i) {
-            const T li = A[i * n + i];
+            const T li = A[i * ld + i];
             if (li < lj || (li == lj && i < j)) ++rank;
         }
         w[rank] = (TO)lj;
-        for (int i = 0; i < n; ++i) Vs[i * n + rank] = (TO)V[i * n + j];
+        for (int i = 0; i < n; ++i) Vs[i * ldo + rank] = (TO)V[i * ld + j];
     }
     __syncthreads();
 }
@@ -181,30 +189,49 @@ __device__ int dev_chol_inv(int n, const double *G, int ldg, double *R, double *
     return bad;
 }
 
+// C (rows x cols, stride ldc) = op(A) op(B) in precision TA, one output per thread step.
+// transA: A stored (inner x rows), else (rows x inner); B stored (inner x cols).
+template <typename TC, typename TA, typename TB>
+__device__ void dev_matmul(int rows, int cols, int inner, const TA *A, int lda, bool transA, const TB *B, int ldb,
+                           TC *C, int ldc)
+{
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+        const int i = e / cols, j = e - (e / cols) * cols;
+        TC acc = (TC)0;
+        if (transA)
+            for (int m = 0; m < inner; ++m) acc += (TC)A[m * lda + i] * (TC)B[m * ldb + j];
+        else
+            for (int m = 0; m < inner; ++m) acc += (TC)A[i * lda + m] * (TC)B[m * ldb + j];
+        C[i * ldc + j] = acc;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------
 // Symmetric eigendecomposition (FP64 Jacobi) of G (n x n, ld ldg): w ascending, Z
-// (n x n) eigenvectors in columns.  A and V live in shared memory when they fit.
+// (n x n, stride n) eigenvectors in columns.  A and V live in shared memory for n <= 64.
 __global__ void __launch_bounds__(kSmallThreads) k_small_eig(int n, const double *G, int64_t ldg, double *w,
                                                              double *Z, double *work, int in_smem)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_rot;
+    __shared__ double cs[kMaxW + 2];
+    __shared__ int pairs[kMaxW + 2];
+    const int ld = pad_ld(n);
     double *A = in_smem ? reinterpret_cast<double *>(smem_raw) : work;
-    double *V = A + n * n;
-    double *cs = in_smem ? V + n * n : work + 2 * n * n;
-    int *pairs = reinterpret_cast<int *>(cs + n + 2);
+    double *V = A + n * ld;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
-        A[e] = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
+        A[i * ld + j] = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
     }
     __syncthreads();
-    dev_jacobi<double>(n, A, V, cs, pairs, &s_rot, kMaxSweeps);
-    dev_sort_eig<double, double>(n, A, V, w, Z);
+    dev_jacobi<double>(n, ld, A, V, cs, pairs, &s_rot, kMaxSweeps);
+    dev_sort_eig<double, double>(n, ld, A, V, w, Z, n);
 }
 
-static size_t eig_smem_bytes(int n) { return (size_t)(2 * n * n + 2 * n + 8) * sizeof(double); }
+static size_t eig_smem_bytes(int n) { return (size_t)2 * n * pad_ld(n) * sizeof(double); }
 
-size_t small_eig_work_doubles(int n) { return (size_t)2 * n * n + 2 * n + 8; }
+size_t small_eig_work_doubles(int n) { return (size_t)2 * n * pad_ld(n) + 8; }
 
 int small_eig(int n, const double *G, int64_t ldg, double *w, double *Z, double *work, cudaStream_t st)
 {
@@ -237,12 +264,12 @@ int small_chol_inv(int n, const double *G, int64_t ldg, double *Rinv, double *wo
 //   D = diag(G_S)^-1/2, eig(D G_S D) = U L U^T, keep L_i > tau max L,
 //   C_S = D U_keep L_keep^-1/2, eig(C_S^T G_A C_S) = Z theta,
 //   coef = C_S Z[:, first k]  (the k smallest; the k largest, descending, if 'largest').
-// T is the precision of the two eigensolves.  With T = float a k-dimensional FP64
-// refinement follows: Y = C_S Z_k, Y <- Y R^-1 with R^T R = Z_k^T Z_k, M = Y^T G_A Y,
-// eig(M) = Q mu (FP64), coef = Y Q.
-// info[0] = kept directions, info[1] = 1 on NaN/Inf or a failed refinement.
+// T is the precision of the two w x w eigensolves.  With T = float a k-dimensional FP64
+// refinement follows: Y = C_S Z_k R^-1 (R^T R = Z_k^T Z_k), M = Y^T G_A Y, eig(M) = Q mu
+// (FP64), coef = Y Q.  info[0] = kept directions, info[1] = 1 on NaN/Inf or a failed
+// refinement.
 
-size_t small_rr_work_doubles(int w) { return (size_t)12 * w * w + 16 * w + 64; }
+size_t small_rr_work_doubles(int w) { return (size_t)16 * w * w + 16 * w + 256; }
 
 template <typename T>
 __device__ void rr_body(int w, int k, int largest, const double *GS, const double *GA, double tau, double *coef,
@@ -250,38 +277,33 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     __shared__ int s_rot, s_keep, s_first, s_flag;
-    // carve the FP64 workspace
-    double *dsc = work;                  // w
-    double *lam = dsc + w;               // w
-    double *Cs = lam + w;                // w x w (ld w; keep columns used)
-    T *U = reinterpret_cast<T *>(Cs + w * w);  // w x w
-    T *T2 = U + w * w;                   // w x w
-    T *Z = T2 + w * w;                   // w x w (keep x keep, ld keep)
-    // rotation parameters of one Jacobi round live in shared memory: every element
-    // update of the round reads them
     __shared__ T csb[kMaxW + 2];
     __shared__ int pairs[kMaxW + 2];
     __shared__ double cs64[kMaxK + 2];
     __shared__ int pairs64[kMaxK + 2];
-    double *dbase = reinterpret_cast<double *>(Z + w * w);
-    dbase = reinterpret_cast<double *>(((uintptr_t)dbase + 15) & ~(uintptr_t)15);
-    double *Zk = dbase;                  // keep x k
-    double *Y = Zk + w * k;              // w x k
-    double *B = Y + w * k;               // w x k
-    double *M = B + w * k;               // k x k
-    double *R = M + k * k;               // k x k
-    double *Ri = R + k * k;              // k x k
-    double *Q = Ri + k * k;              // k x k
-    double *mu = Q + k * k;              // k
-    double *A64g = mu + k;               // k x k (global fallback)
-    double *V64g = A64g + k * k;         // k x k
-    T *Ag = reinterpret_cast<T *>(((uintptr_t)(V64g + k * k) + 15) & ~(uintptr_t)15);
+    const int ld = pad_ld(w);
+    // FP64 workspace
+    double *dsc = work;                       // w
+    double *GAs = dsc + w;                    // w x w, symmetrised G_A
+    double *Cs = GAs + w * w;                 // w x w (keep columns used)
+    double *Zk = Cs + w * w;                  // w x k
+    double *ZR = Zk + w * k;                  // w x k
+    double *Y = ZR + w * k;                   // w x k
+    double *Bm = Y + w * k;                   // w x k
+    double *M = Bm + w * k;                   // k x k
+    double *R = M + k * k;                    // k x k
+    double *Ri = R + k * k;                   // k x k
+    double *Q = Ri + k * k;                   // k x k
+    double *mu = Q + k * k;                   // k
+    T *lam = reinterpret_cast<T *>(mu + k);   // w
+    T *GAt = lam + w + 2;                     // w x w
+    T *Cst = GAt + w * w;                     // w x w
+    T *U = Cst + w * w;                       // w x w
+    T *T2 = U + w * w;                        // w x w
+    T *Z = T2 + w * w;                        // w x w
+    T *Ag = reinterpret_cast<T *>(((uintptr_t)(Z + w * w) + 15) & ~(uintptr_t)15);
     T *A = use_smem ? As : Ag;
-    T *V = use_smem ? Vs : Ag + w * w;
-    // the k x k FP64 refinement reuses the shared region once the w x w solves are done
-    const bool ref_smem = use_smem && (size_t)2 * k * k * sizeof(double) <= (size_t)2 * w * w * sizeof(T);
-    double *A64 = ref_smem ? reinterpret_cast<double *>(As) : A64g;
-    double *V64 = A64 + k * k;
+    T *V = use_smem ? Vs : Ag + w * ld;
 
     for (int i = tid; i < w; i += nt) {
         const double d = GS[i * w + i];
@@ -289,18 +311,20 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
     }
     __syncthreads();
     for (int e = tid; e < w * w; e += nt) {
-        const int i = e / w, j = e % w;
-        A[e] = (T)(dsc[i] * 0.5 * (GS[i * w + j] + GS[j * w + i]) * dsc[j]);
+        const int i = e / w, j = e - (e / w) * w;
+        const double g = 0.5 * (GA[i * w + j] + GA[j * w + i]);
+        GAs[e] = g;
+        GAt[e] = (T)g;
+        A[i * ld + j] = (T)(dsc[i] * 0.5 * (GS[i * w + j] + GS[j * w + i]) * dsc[j]);
     }
     __syncthreads();
-    dev_jacobi<T>(w, A, V, csb, pairs, &s_rot, kMaxSweeps);
-    dev_sort_eig<T, T>(w, A, V, reinterpret_cast<T *>(lam), U);
+    dev_jacobi<T>(w, ld, A, V, csb, pairs, &s_rot, kMaxSweeps);
+    dev_sort_eig<T, T>(w, ld, A, V, lam, U, w);
     if (tid == 0) {
-        const T *lt = reinterpret_cast<const T *>(lam);
-        const double lmax = (double)lt[w - 1];
+        const double lmax = (double)lam[w - 1];
         int first = w;
         for (int i = 0; i < w; ++i)
-            if ((double)lt[i] > tau * lmax) {
+            if ((double)lam[i] > tau * lmax) {
                 first = i;
                 break;
             }
@@ -309,45 +333,32 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
     }
     __syncthreads();
     const int first = s_first, keep = s_keep;
-    {
-        const T *lt = reinterpret_cast<const T *>(lam);
-        for (int e = tid; e < w * keep; e += nt) {
-            const int i = e / keep, j = e % keep;
-            Cs[i * w + j] = dsc[i] * (double)U[i * w + first + j] / sqrt((double)lt[first + j]);
-        }
-    }
-    __syncthreads();
-    // T2 = G_A Cs (w x keep) and A = Cs^T T2 (keep x keep, ld keep), in precision T
     for (int e = tid; e < w * keep; e += nt) {
-        const int i = e / keep, j = e % keep;
-        T s = (T)0;
-        for (int m = 0; m < w; ++m) s += (T)(0.5 * (GA[i * w + m] + GA[m * w + i])) * (T)Cs[m * w + j];
-        T2[i * w + j] = s;
+        const int i = e / keep, j = e - (e / keep) * keep;
+        const double c = dsc[i] * (double)U[i * w + first + j] / sqrt((double)lam[first + j]);
+        Cs[i * w + j] = c;
+        Cst[i * w + j] = (T)c;
     }
     __syncthreads();
+    // projected G_A in precision T: T2 = G_A Cs, A = Cs^T T2 (keep x keep, stride ldk)
+    const int ldk = pad_ld(keep);
+    dev_matmul<T, T, T>(w, keep, w, GAt, w, false, Cst, w, T2, w);
+    dev_matmul<T, T, T>(keep, keep, w, Cst, w, true, T2, w, A, ldk);
     for (int e = tid; e < keep * keep; e += nt) {
-        const int i = e / keep, j = e % keep;
-        T s = (T)0;
-        for (int m = 0; m < w; ++m) s += (T)Cs[m * w + i] * T2[m * w + j];
-        A[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < keep * keep; e += nt) {
-        const int i = e / keep, j = e % keep;
+        const int i = e / keep, j = e - (e / keep) * keep;
         if (i < j) {
-            const T a = (T)0.5 * (A[i * keep + j] + A[j * keep + i]);
-            A[i * keep + j] = a;
-            A[j * keep + i] = a;
+            const T a = (T)0.5 * (A[i * ldk + j] + A[j * ldk + i]);
+            A[i * ldk + j] = a;
+            A[j * ldk + i] = a;
         }
     }
     __syncthreads();
-    dev_jacobi<T>(keep, A, V, csb, pairs, &s_rot, kMaxSweeps);
-    T *lam2 = reinterpret_cast<T *>(lam);
-    dev_sort_eig<T, T>(keep, A, V, lam2, Z);
+    dev_jacobi<T>(keep, ldk, A, V, csb, pairs, &s_rot, kMaxSweeps);
+    dev_sort_eig<T, T>(keep, ldk, A, V, lam, Z, keep);
     const int kk = k < keep ? k : keep;
     if (sizeof(T) == sizeof(double)) {
         for (int e = tid; e < w * k; e += nt) {
-            const int i = e / k, j = e % k;
+            const int i = e / k, j = e - (e / k) * k;
             double s = 0.0;
             if (j < kk) {
                 const int col = largest ? keep - 1 - j : j;
@@ -355,71 +366,46 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
             }
             coef[e] = s;
         }
-        for (int j = tid; j < k; j += nt) theta[j] = j < kk ? (double)lam2[largest ? keep - 1 - j : j] : 0.0;
+        for (int j = tid; j < k; j += nt) theta[j] = j < kk ? (double)lam[largest ? keep - 1 - j : j] : 0.0;
         if (tid == 0) {
             info[0] = keep;
             int bad = 0;
             for (int j = 0; j < kk; ++j)
-                if (!isfinite((double)lam2[j])) bad = 1;
+                if (!isfinite((double)lam[j])) bad = 1;
             info[1] = bad;
         }
         return;
     }
     // FP64 refinement of the k-dimensional Ritz subspace
     for (int e = tid; e < keep * kk; e += nt) {
-        const int i = e / kk, j = e % kk;
+        const int i = e / kk, j = e - (e / kk) * kk;
         Zk[e] = (double)Z[i * keep + (largest ? keep - 1 - j : j)];
     }
     __syncthreads();
-    for (int e = tid; e < kk * kk; e += nt) {  // M = Zk^T Zk
-        const int i = e / kk, j = e % kk;
-        double s = 0.0;
-        for (int m = 0; m < keep; ++m) s += Zk[m * kk + i] * Zk[m * kk + j];
-        M[e] = s;
-    }
-    __syncthreads();
+    dev_matmul<double, double, double>(kk, kk, keep, Zk, kk, true, Zk, kk, M, kk);
     const int bad_chol = dev_chol_inv(kk, M, kk, R, Ri, &s_flag);
-    for (int e = tid; e < keep * kk; e += nt) {  // B <- Zk Ri (keep x kk), B as scratch
-        const int i = e / kk, j = e % kk;
-        double s = 0.0;
-        for (int l = 0; l <= j; ++l) s += Zk[i * kk + l] * Ri[l * kk + j];
-        B[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < w * kk; e += nt) {  // Y = Cs (Zk Ri)
-        const int i = e / kk, j = e % kk;
-        double s = 0.0;
-        for (int m = 0; m < keep; ++m) s += Cs[i * w + m] * B[m * kk + j];
-        Y[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < w * kk; e += nt) {  // B = G_A Y
-        const int i = e / kk, j = e % kk;
-        double s = 0.0;
-        for (int m = 0; m < w; ++m) s += 0.5 * (GA[i * w + m] + GA[m * w + i]) * Y[m * kk + j];
-        B[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < kk * kk; e += nt) {  // A64 = Y^T B
-        const int i = e / kk, j = e % kk;
-        double s = 0.0;
-        for (int m = 0; m < w; ++m) s += Y[m * kk + i] * B[m * kk + j];
-        A64[e] = s;
-    }
-    __syncthreads();
+    dev_matmul<double, double, double>(keep, kk, kk, Zk, kk, false, Ri, kk, ZR, kk);
+    dev_matmul<double, double, double>(w, kk, keep, Cs, w, false, ZR, kk, Y, kk);
+    dev_matmul<double, double, double>(w, kk, w, GAs, w, false, Y, kk, Bm, kk);
+    // the k x k projection reuses the shared region (the w x w solves are done)
+    const int ldkk = pad_ld(kk);
+    const bool ref_smem = use_smem && (size_t)2 * kk * ldkk * sizeof(double) <= (size_t)2 * w * ld * sizeof(T);
+    double *A64 = ref_smem ? reinterpret_cast<double *>(As) : reinterpret_cast<double *>(Ag);
+    double *V64 = A64 + kk * ldkk;
+    dev_matmul<double, double, double>(kk, kk, w, Y, kk, true, Bm, kk, A64, ldkk);
     for (int e = tid; e < kk * kk; e += nt) {
-        const int i = e / kk, j = e % kk;
+        const int i = e / kk, j = e - (e / kk) * kk;
         if (i < j) {
-            const double a = 0.5 * (A64[i * kk + j] + A64[j * kk + i]);
-            A64[i * kk + j] = a;
-            A64[j * kk + i] = a;
+            const double a = 0.5 * (A64[i * ldkk + j] + A64[j * ldkk + i]);
+            A64[i * ldkk + j] = a;
+            A64[j * ldkk + i] = a;
         }
     }
     __syncthreads();
-    dev_jacobi<double>(kk, A64, V64, cs64, pairs64, &s_rot, kMaxSweeps);
-    dev_sort_eig<double, double>(kk, A64, V64, mu, Q);
+    dev_jacobi<double>(kk, ldkk, A64, V64, cs64, pairs64, &s_rot, kMaxSweeps);
+    dev_sort_eig<double, double>(kk, ldkk, A64, V64, mu, Q, kk);
     for (int e = tid; e < w * k; e += nt) {  // coef = Y Q (descending for 'largest')
-        const int i = e / k, j = e % k;
+        const int i = e / k, j = e - (e / k) * k;
         double s = 0.0;
         if (j < kk) {
             const int col = largest ? kk - 1 - j : j;
@@ -444,7 +430,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_rr(int w, int k, int la
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);
-    T *Vs = As + w * w;
+    T *Vs = As + w * pad_ld(w);
     rr_body<T>(w, k, largest, GS, GA, tau, coef, theta, work, info, As, Vs, use_smem);
 }
 
@@ -459,7 +445,7 @@ int small_svqb_rr(int w, int k, int largest, int mixed, const double *GS, const 
         attr = true;
     }
     const size_t es = mixed ? sizeof(float) : sizeof(double);
-    const size_t sm = 2 * (size_t)w * w * es;
+    const size_t sm = 2 * (size_t)w * pad_ld(w) * es;
     const int use_smem = sm <= (size_t)cap;
     if (mixed)
         k_small_rr<float><<<1, kSmallThreads, use_smem ? sm : 0, st>>>(w, k, largest, GS, GA, tau, coef, theta,
