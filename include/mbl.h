@@ -105,6 +105,10 @@ int mbl_hamiltonian_apply(const mbl_chain *chain, double sigma, int dtype, const
  * concurrent products. */
 int mbl_set_product_tile_bits(int k, int dtype, int bits);
 
+/* Tuning: bytes of each row that one lane moves per neighbour in the tiled product
+ * (16 or 32; 0 = default 32) for block width k and type dtype. */
+int mbl_set_product_lane_bytes(int k, int dtype, int bytes);
+
 /* ---- folded-spectrum LOBPCG (Sec. 3.2, Sec. 6.2) ---------------------------------- */
 
 typedef struct {
@@ -176,6 +180,30 @@ int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts
 int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
                              const double *X0_dev, double *evals_host, double *evecs_dev,
                              double *resid_host, mbl_lobpcg_stats *stats, mbl_stream_t stream);
+
+/* Batched disorder averaging (Sec. 3.1: realisations and disorder strengths are
+ * independent levels of concurrency): nprob problems, any mix of L and fields, solved
+ * with the same opts.  nstreams worker threads each drive one CUDA stream and one
+ * workspace slot and take problems in order; each problem runs mbl_lobpcg_solve (with
+ * captured iterations when opts->use_graph) on its worker's stream, so small problems
+ * overlap on the GPU.  The workers start after the work already queued on `stream`, and
+ * the call returns when every problem has finished.
+ *   sigmas:   nprob shifts, or NULL: sigma_i = (E_min + E_max)/2 of problem i from
+ *             LOBPCG bounds on +-H (block 4, tolerance 1e-7, started from the first four
+ *             columns of its X0 block); then, if opts->norm_h <= 0, ||H|| = max |E|.
+ *   X0_dev:   the problems' n_i x k FP64 start blocks packed one after another.
+ *   workspace: mbl_batched_workspace_size bytes (nstreams slots of the largest problem).
+ *   evals_host, resid_host: nprob x nev (problem-major); evecs_dev: the n_i x nev blocks
+ *   packed one after another, or NULL; stats: nprob entries or NULL.
+ * Returns MBL_OK, MBL_ERR_NOT_CONVERGED when some problem did not converge (all outputs
+ * written), or the first error met (remaining problems are skipped). */
+int mbl_batched_workspace_size(int nprob, const mbl_chain *chains, const mbl_lobpcg_opts *opts,
+                               int nstreams, size_t *bytes);
+int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, const double *sigmas,
+                             const mbl_lobpcg_opts *opts, const double *X0_dev, int nstreams,
+                             void *workspace_dev, size_t workspace_bytes, double *evals_host,
+                             double *evecs_dev, double *resid_host, mbl_lobpcg_stats *stats,
+                             mbl_stream_t stream);
 
 /* Spectrum bounds E_min, E_max of the sector Hamiltonian (used to place sigma at the
  * middle of the spectrum and to scale tolerances): unpreconditioned LOBPCG on +H and

@@ -31,7 +31,8 @@ MODE_MIXED = 1
 EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis_rank",
             "mbl_hamiltonian_apply", "mbl_lobpcg_workspace_size", "mbl_lobpcg_solve",
             "mbl_bounds_workspace_size", "mbl_spectrum_bounds", "mbl_lobpcg_solve_noalloc",
-            "mbl_set_product_tile_bits")
+            "mbl_set_product_tile_bits", "mbl_set_product_lane_bytes", "mbl_batched_workspace_size",
+            "mbl_lobpcg_solve_batched")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -83,6 +84,13 @@ def lib():
     so.mbl_basis_rank.argtypes = [i32, i32, p, p, i64, p]
     so.mbl_hamiltonian_apply.restype = i32
     so.mbl_hamiltonian_apply.argtypes = [pch, f64, i32, p, i64, p, i64, i64, i32, p]
+    so.mbl_batched_workspace_size.restype = i32
+    so.mbl_batched_workspace_size.argtypes = [i32, pch, popt, i32, ctypes.POINTER(sz)]
+    so.mbl_lobpcg_solve_batched.restype = i32
+    so.mbl_lobpcg_solve_batched.argtypes = [i32, pch, p, popt, p, i32, p, sz, p, p, p,
+                                            ctypes.POINTER(LobpcgStats), p]
+    so.mbl_set_product_lane_bytes.restype = i32
+    so.mbl_set_product_lane_bytes.argtypes = [i32, i32, i32]
     so.mbl_set_product_tile_bits.restype = i32
     so.mbl_set_product_tile_bits.argtypes = [i32, i32, i32]
     so.mbl_lobpcg_workspace_size.restype = i32
@@ -187,6 +195,13 @@ def set_product_tile_bits(k, dtype, bits):
     _check(lib().mbl_set_product_tile_bits(int(k), dt, int(bits)), "mbl_set_product_tile_bits")
 
 
+def set_product_lane_bytes(k, dtype, nbytes):
+    """Bytes per lane per neighbour row in the tiled product (16, 32, or 0 = default)."""
+    torch = _torch()
+    dt = MBL_F32 if dtype == torch.float32 else MBL_F64
+    _check(lib().mbl_set_product_lane_bytes(int(k), dt, int(nbytes)), "mbl_set_product_lane_bytes")
+
+
 def make_opts(nev, k, tol=1e-8, max_iter=200, pcg_iters=50, pcg_tol=0.0, norm_h=0.0,
               mode=MODE_MIXED, use_graph=1, timing=0):
     return LobpcgOpts(int(nev), int(k), int(max_iter), int(pcg_iters), float(tol), float(pcg_tol),
@@ -245,6 +260,46 @@ def lobpcg_solve_noalloc(chain, sigma, opts, X0, evecs=None, allow_not_converged
                                         _stream_ptr(X0))
     _check(rc, "mbl_lobpcg_solve_noalloc", ok)
     return evals, resid, stats.as_dict(), rc
+
+
+def chain_array(chains):
+    """A contiguous C array of mbl_chain structs (keeps the field arrays alive)."""
+    arr = (Chain * len(chains))(*chains)
+    arr._keep = [c._keep for c in chains]
+    return arr
+
+
+def batched_workspace_size(chains, opts, nstreams):
+    arr = chain_array(chains)
+    out = ctypes.c_size_t(0)
+    _check(lib().mbl_batched_workspace_size(len(chains), arr, ctypes.byref(opts), int(nstreams),
+                                            ctypes.byref(out)), "mbl_batched_workspace_size")
+    return int(out.value)
+
+
+def lobpcg_solve_batched(chains, opts, X0, workspace, nstreams, sigmas=None, evecs=None,
+                         allow_not_converged=False):
+    """mbl_lobpcg_solve_batched.  X0: (sum n_i) x k float64 CUDA tensor (the problems'
+    start blocks stacked); evecs: optional (sum n_i) x nev tensor.  Returns (evals
+    nprob x nev, resid nprob x nev, list of stats dicts, status)."""
+    torch = _torch()
+    nprob, nev = len(chains), opts.nev
+    arr = chain_array(chains)
+    evals = np.zeros((nprob, nev), dtype=np.float64)
+    resid = np.zeros((nprob, nev), dtype=np.float64)
+    stats = (LobpcgStats * nprob)()
+    sg = None
+    if sigmas is not None:
+        sg_arr = np.ascontiguousarray(np.asarray(sigmas, dtype=np.float64))
+        sg = sg_arr.ctypes.data_as(ctypes.c_void_p)
+    ev_ptr = _dev(evecs, torch.float64, "evecs") if evecs is not None else None
+    ok = (MBL_OK, MBL_ERR_NOT_CONVERGED) if allow_not_converged else (MBL_OK,)
+    rc = lib().mbl_lobpcg_solve_batched(nprob, arr, sg, ctypes.byref(opts), _dev(X0, torch.float64, "X0"),
+                                        int(nstreams), _dev(workspace, torch.uint8, "workspace"),
+                                        workspace.numel(), evals.ctypes.data_as(ctypes.c_void_p), ev_ptr,
+                                        resid.ctypes.data_as(ctypes.c_void_p), stats, _stream_ptr(X0))
+    _check(rc, "mbl_lobpcg_solve_batched", ok)
+    return evals, resid, [st.as_dict() for st in stats], rc
 
 
 def bounds_workspace_size(chain, k):

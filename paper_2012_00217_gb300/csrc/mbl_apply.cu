@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -38,11 +39,11 @@ struct RowLayout {
     static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
 };
 
-// Tiled kernels move up to 32 bytes per lane (two 16-byte loads per neighbour row).
-template <typename T, int K>
+// Tiled kernels move up to LB bytes per lane (LB = 16 or 32) of every neighbour row.
+template <typename T, int K, int LB = 32>
 struct WideRowLayout {
     static constexpr int kBytes = K * (int)sizeof(T);
-    static constexpr int V = kBytes >= 32 ? 32 / (int)sizeof(T) : (kBytes >= 16 ? 16 / (int)sizeof(T) : K);
+    static constexpr int V = kBytes >= LB ? LB / (int)sizeof(T) : (kBytes >= 16 ? 16 / (int)sizeof(T) : K);
     static constexpr int G = K / V;
     static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
 };
@@ -428,13 +429,13 @@ static __device__ LowRec g_lowtab[kLowRecords];
 
 __host__ __device__ inline int lowtab_base(int B) { return (1 << B) - 4; }
 
-template <typename T, int K, int MODE>
+template <typename T, int K, int MODE, int LB>
 __global__ void __launch_bounds__(kThreads, 3) k_apply_tiled(ChainParams cp, int B, const T *__restrict__ X,
                                                           int64_t ldx, T *__restrict__ Y, int64_t ldy,
                                                           T *__restrict__ R, const T *__restrict__ dinv,
                                                           PcgScalars ps, Reduce rd)
 {
-    using Lay = WideRowLayout<T, K>;
+    using Lay = WideRowLayout<T, K, LB>;
     constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G, CH = 32;
     __shared__ uint32_t sbin[kBinomDim * kBinomDim];
     __shared__ T tab[1024];
@@ -945,16 +946,16 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update_generic(uint32_t n, int
 // ---------------------------------------------------------------------------------
 // Host-side dispatch.
 
-static int g_num_sms = 0;
+static std::atomic<int> g_num_sms{0};
 
 int num_sms()
 {
-    if (g_num_sms == 0) {
+    if (g_num_sms.load() == 0) {
         int dev = 0, v = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-        g_num_sms = v;
+        g_num_sms.store(v);
     }
-    return g_num_sms;
+    return g_num_sms.load();
 }
 
 int make_chain_params(const mbl_chain *chain, double sigma, ChainParams *cp)
@@ -995,11 +996,11 @@ static cudaError_t launch_apply_k(const ChainParams &cp, const T *X, int64_t ldx
 {
     auto kern = k_apply<T, K, MODE>;
     const size_t sm = apply_smem_bytes<T>();
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set_once = [&]() {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set_once;
     kern<<<grid, kThreads, sm, st>>>(cp, X, ldx, Y, ldy, n, R, dinv, ps, rd);
     return cudaGetLastError();
 }
@@ -1009,6 +1010,7 @@ static cudaError_t launch_apply_k(const ChainParams &cp, const T *X, int64_t ldx
 // Tile width override per (block width, element size): 0 = heuristic, -1 = untiled,
 // >= 2 = that many low bits.  Set by the autotuner.
 static int g_tile_bits[2][8] = {};
+static int g_lane_bytes[2][8] = {};  // 0: default (32), else 16 or 32
 
 static int kslot(int K)
 {
@@ -1032,13 +1034,14 @@ uint32_t host_binom(int n, int k)
     return (uint32_t)c;
 }
 
-// Tile width heuristic: tiles of at least 64 rows (B >= 8) keep the 32-row work items
-// full; B <= L - 2 keeps at least two high bits.
+// Tile width heuristic: the widest table-backed tiles (B = 13, at most L - 2 so that two
+// high bits remain); measured fastest or within a few per cent of it for L = 20..26,
+// k = 8..64 (wider tiles leave more bonds inside the tile).
 static int heuristic_tile_bits(int L, int K, size_t es)
 {
     (void)K;
     (void)es;
-    int B = 8;
+    int B = kLowMaxB;
     if (B > L - 2) B = L - 2;
     return B >= 2 ? B : -1;
 }
@@ -1055,19 +1058,25 @@ int tile_bits_for(int L, int K, size_t es)
 }
 
 void set_tile_bits(int K, size_t es, int bits) { g_tile_bits[es == 8 ? 1 : 0][kslot(K)] = bits; }
+void set_lane_bytes(int K, size_t es, int bytes) { g_lane_bytes[es == 8 ? 1 : 0][kslot(K)] = bytes; }
+static int lane_bytes_for(int K, size_t es)
+{
+    const int v = g_lane_bytes[es == 8 ? 1 : 0][kslot(K)];
+    return v == 16 ? 16 : 32;
+}
 
-template <typename T, int K, int MODE>
-static cudaError_t launch_tiled(const ChainParams &cp, int B, const T *X, int64_t ldx, T *Y, int64_t ldy, T *R,
-                                const T *dinv, const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
+template <typename T, int K, int MODE, int LB>
+static cudaError_t launch_tiled_lb(const ChainParams &cp, int B, const T *X, int64_t ldx, T *Y, int64_t ldy, T *R,
+                                   const T *dinv, const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
 {
     if (ensure_lowtab(B) != MBL_OK) return cudaErrorUnknown;
-    auto kern = k_apply_tiled<T, K, MODE>;
-    static int per_sm = 0;
-    if (per_sm == 0) {
+    auto kern = k_apply_tiled<T, K, MODE, LB>;
+    static const int per_sm = [&]() {
+        int v = 0;
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
-            per_sm = 1;
-    }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kThreads, 0) != cudaSuccess || v < 1) v = 1;
+        return v;
+    }();
     const uint32_t rmax = host_binom(B, B / 2);
     const int64_t items = ((int64_t)1 << (cp.L - B)) * (int64_t)((rmax + 31) / 32);
     int64_t grid = (int64_t)num_sms() * per_sm;
@@ -1076,6 +1085,15 @@ static cudaError_t launch_tiled(const ChainParams &cp, int B, const T *X, int64_
     if (grid > need) grid = need;
     kern<<<(int)grid, kThreads, 0, st>>>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd);
     return cudaGetLastError();
+}
+
+template <typename T, int K, int MODE>
+static cudaError_t launch_tiled(const ChainParams &cp, int B, const T *X, int64_t ldx, T *Y, int64_t ldy, T *R,
+                                const T *dinv, const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
+{
+    if (lane_bytes_for(K, sizeof(T)) == 16)
+        return launch_tiled_lb<T, K, MODE, 16>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd, st);
+    return launch_tiled_lb<T, K, MODE, 32>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd, st);
 }
 
 static int apply_grid(uint32_t n, int cap_per_sm)
@@ -1087,10 +1105,10 @@ static int apply_grid(uint32_t n, int cap_per_sm)
 }
 
 template <typename T>
-static bool vec_ok_wide(const void *p, int64_t ld, int K)
+static bool vec_ok_wide(const void *p, int64_t ld, int K, int lb)
 {
     const int bytes = K * (int)sizeof(T);
-    const int align = bytes >= 32 ? 32 : (bytes >= 16 ? 16 : bytes);
+    const int align = bytes >= lb ? lb : (bytes >= 16 ? 16 : bytes);
     return ((uintptr_t)p % align == 0) && ((ld * (int64_t)sizeof(T)) % align == 0);
 }
 
@@ -1112,7 +1130,8 @@ static int dispatch_plain(const ChainParams &cp, const T *X, int64_t ldx, T *Y, 
     cudaError_t e = cudaSuccess;
     bool done = true;
     const int B = tile_bits_for(cp.L, k, sizeof(T));
-    if (B >= 2 && vec_ok_wide<T>(X, ldx, k) && vec_ok_wide<T>(Y, ldy, k)) {
+    const int lb = lane_bytes_for(k, sizeof(T));
+    if (B >= 2 && vec_ok_wide<T>(X, ldx, k, lb) && vec_ok_wide<T>(Y, ldy, k, lb)) {
         switch (k) {
         case 1: e = launch_tiled<T, 1, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
         case 2: e = launch_tiled<T, 2, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
@@ -1139,11 +1158,11 @@ static int dispatch_plain(const ChainParams &cp, const T *X, int64_t ldx, T *Y, 
     }
     if (!done) {
         const size_t sm = apply_smem_bytes<T>();
-        static bool attr_set = false;
-        if (!attr_set) {
+        static const bool attr_set_once = [&]() {
             cudaFuncSetAttribute(k_apply_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            attr_set = true;
-        }
+            return true;
+        }();
+        (void)attr_set_once;
         k_apply_generic<T><<<grid, kThreads, sm, st>>>(cp, X, ldx, Y, ldy, n, k);
         e = cudaGetLastError();
     }
@@ -1236,12 +1255,12 @@ int pcg_step(const ChainParams &cp, uint32_t n, int k, const T *dinv, T *r, T *p
     case 64: e = pcg_step_k<T, 64>(cp, n, dinv, r, p, t, w, ps, rd, grid, st); break;
     default: {
         const size_t sm = apply_smem_bytes<T>();
-        static bool attr_set = false;
-        if (!attr_set) {
+        static const bool attr_set_once = [&]() {
             cudaFuncSetAttribute(k_apply_pcg_generic<T, kPcgT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             cudaFuncSetAttribute(k_apply_pcg_generic<T, kPcgQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            attr_set = true;
-        }
+            return true;
+        }();
+        (void)attr_set_once;
         k_apply_pcg_generic<T, kPcgT><<<grid, kThreads, sm, st>>>(cp, p, t, n, k, nullptr, dinv, ps, rd);
         k_apply_pcg_generic<T, kPcgQ><<<grid, kThreads, sm, st>>>(cp, t, nullptr, n, k, r, dinv, ps, rd);
         int ugrid = num_sms() * 8;
@@ -1266,6 +1285,14 @@ extern "C" int mbl_set_product_tile_bits(int k, int dtype, int bits)
     if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || bits < -1 || bits > 16 || bits == 1)
         return MBL_ERR_ARG;
     mbl::set_tile_bits(k, dtype == MBL_F32 ? 4 : 8, bits);
+    return MBL_OK;
+}
+
+extern "C" int mbl_set_product_lane_bytes(int k, int dtype, int bytes)
+{
+    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || (bytes != 0 && bytes != 16 && bytes != 32))
+        return MBL_ERR_ARG;
+    mbl::set_lane_bytes(k, dtype == MBL_F32 ? 4 : 8, bytes);
     return MBL_OK;
 }
 

@@ -197,14 +197,14 @@ int update(const double *A, int64_t lda, int p, const double *M, int64_t ldm, in
     int64_t blocks = (n + 31) / 32;
     const int64_t cap = (int64_t)num_sms() * 4;
     if (blocks > cap) blocks = cap;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set_once = [&]() {
         // largest use: p = 192, q = 64 -> (192 * 64 + 32 * 192) doubles = 144 KB
         const int mx = (192 * 64 + 32 * 192) * (int)sizeof(double);
         cudaFuncSetAttribute(k_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set_once;
     if (compute_f32) {
         const size_t sm = (size_t)(p * q + 32 * p) * sizeof(float);
         k_update<float><<<(int)blocks, 256, sm, st>>>(A, lda, p, M, ldm, q, C, ldc, D, ldd, n, alpha, beta);

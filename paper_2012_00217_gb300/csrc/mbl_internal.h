@@ -33,6 +33,7 @@ size_t pcg_partial_doubles();
 // element size es; -1 = untiled kernel.  set_tile_bits: 0 heuristic, -1 untiled, >= 2 fixed.
 int tile_bits_for(int L, int K, size_t es);
 void set_tile_bits(int K, size_t es, int bits);
+void set_lane_bytes(int K, size_t es, int bytes);
 template <typename T>
 int pcg_fold_dinv(const ChainParams &cp, uint32_t n, T *dinv, cudaStream_t st);
 template <typename T>

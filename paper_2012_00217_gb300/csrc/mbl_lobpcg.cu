@@ -19,9 +19,13 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <mutex>
+#include <thread>
+#include <vector>
 
 #include "mbl_dense.h"
 #include "mbl_device.cuh"
@@ -549,8 +553,8 @@ extern "C" int mbl_bounds_workspace_size(const mbl_chain *chain, int k, size_t *
     return MBL_OK;
 }
 
-static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, const double *X0, void *ws,
-                      size_t ws_bytes, int largest, double *theta_out, int *iters, cudaStream_t st)
+static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, const double *X0, int64_t ldx0,
+                      void *ws, size_t ws_bytes, int largest, double *theta_out, int *iters, cudaStream_t st)
 {
     int64_t n = mbl_basis_size(chain->L, chain->n_up);
     Solver s;
@@ -572,7 +576,7 @@ static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, c
         return MBL_ERR_CUDA;
     MBL_TRY(mbl_basis_build(chain->L, chain->n_up, s.b.states, n, (mbl_stream_t)st));
     s.cp.states = s.b.states;
-    MBL_TRY(s.cholqr_into_x(X0, k));
+    MBL_TRY(s.cholqr_into_x(X0, ldx0));
     MBL_TRY(s.refresh_tx());
     MBL_TRY(initial_rr(s));
     MBL_TRY(s.enqueue_bounds_status());
@@ -609,10 +613,10 @@ extern "C" int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, in
     if (rc != MBL_OK) return rc;
     if (iters_host) *iters_host = 0;
     double lo = 0.0, hi = 0.0;
-    int r1 = bounds_one(chain, k, tol, max_iter, X0_dev, workspace_dev, workspace_bytes, 0, &lo, iters_host,
+    int r1 = bounds_one(chain, k, tol, max_iter, X0_dev, k, workspace_dev, workspace_bytes, 0, &lo, iters_host,
                         (cudaStream_t)stream);
     if (r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) return r1;
-    int r2 = bounds_one(chain, k, tol, max_iter, X0_dev, workspace_dev, workspace_bytes, 1, &hi, iters_host,
+    int r2 = bounds_one(chain, k, tol, max_iter, X0_dev, k, workspace_dev, workspace_bytes, 1, &hi, iters_host,
                         (cudaStream_t)stream);
     if (r2 != MBL_OK && r2 != MBL_ERR_NOT_CONVERGED) return r2;
     if (emin_host) *emin_host = lo;
@@ -670,4 +674,142 @@ extern "C" int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, co
     o.timing = 0;
     return mbl_lobpcg_solve(chain, sigma, &o, X0_dev, ws, kNoAllocBytes, evals_host, evecs_dev, resid_host, stats,
                             stream);
+}
+
+// ------------------------------------------------------------------------------------
+// Batched solve: many disorder realisations (any mix of L) in flight at once.  Each of
+// nstreams worker threads owns a stream and one workspace slot, takes the next problem,
+// finds sigma and ||H|| from its spectrum bounds when they are not given, and runs the
+// single-problem solve (whose iterations are captured CUDA graphs) on its stream.
+
+namespace {
+
+constexpr int kBatchBoundsK = 4;
+constexpr double kBatchBoundsTol = 1e-7;
+
+size_t batch_slot_bytes(int nprob, const mbl_chain *chains, const mbl_lobpcg_opts *opts, int *rc)
+{
+    size_t slot = 0;
+    *rc = MBL_OK;
+    for (int i = 0; i < nprob; ++i) {
+        size_t a = 0, b = 0;
+        int r = mbl_lobpcg_workspace_size(&chains[i], opts, &a);
+        if (r != MBL_OK) {
+            *rc = r;
+            return 0;
+        }
+        if (mbl_bounds_workspace_size(&chains[i], kBatchBoundsK, &b) != MBL_OK) b = 0;
+        slot = std::max(slot, std::max(a, b));
+    }
+    return align_up(slot);
+}
+
+}  // namespace
+
+extern "C" int mbl_batched_workspace_size(int nprob, const mbl_chain *chains, const mbl_lobpcg_opts *opts,
+                                          int nstreams, size_t *bytes)
+{
+    if (nprob < 1 || !chains || !opts || !bytes || nstreams < 1 || nstreams > 64) return MBL_ERR_ARG;
+    int rc;
+    const size_t slot = batch_slot_bytes(nprob, chains, opts, &rc);
+    if (rc != MBL_OK) return rc;
+    *bytes = slot * (size_t)std::min(nstreams, nprob);
+    return MBL_OK;
+}
+
+extern "C" int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, const double *sigmas,
+                                        const mbl_lobpcg_opts *opts, const double *X0_dev, int nstreams,
+                                        void *workspace_dev, size_t workspace_bytes, double *evals_host,
+                                        double *evecs_dev, double *resid_host, mbl_lobpcg_stats *stats,
+                                        mbl_stream_t stream)
+{
+    if (nprob < 1 || !chains || !opts || !X0_dev || !workspace_dev || nstreams < 1 || nstreams > 64)
+        return MBL_ERR_ARG;
+    if ((uintptr_t)workspace_dev % kAlign) return MBL_ERR_ARG;
+    int rc;
+    const size_t slot = batch_slot_bytes(nprob, chains, opts, &rc);
+    if (rc != MBL_OK) return rc;
+    const int ns = std::min(nstreams, nprob);
+    if (workspace_bytes < slot * (size_t)ns) return MBL_ERR_WORKSPACE;
+    if (opts->use_graph == 0 && opts->timing) return MBL_ERR_ARG;
+    // packed offsets of each problem's start block and eigenvectors
+    std::vector<int64_t> off_x(nprob + 1, 0), off_v(nprob + 1, 0);
+    for (int i = 0; i < nprob; ++i) {
+        const int64_t n = mbl_basis_size(chains[i].L, chains[i].n_up);
+        if (n <= 0 || (sigmas == nullptr && chains[i].L < 2)) return MBL_ERR_ARG;
+        off_x[i + 1] = off_x[i] + n * opts->k;
+        off_v[i + 1] = off_v[i] + n * opts->nev;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MBL_ERR_CUDA;
+    // the workers start after the caller's prior work on its stream
+    cudaEvent_t start_ev;
+    if (cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) != cudaSuccess) return MBL_ERR_CUDA;
+    if (cudaEventRecord(start_ev, (cudaStream_t)stream) != cudaSuccess) {
+        cudaEventDestroy(start_ev);
+        return MBL_ERR_CUDA;
+    }
+    std::atomic<int> next{0};
+    std::atomic<int> first_error{MBL_OK};
+    std::atomic<int> not_converged{0};
+    auto worker = [&](int wid) {
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            first_error.store(MBL_ERR_CUDA);
+            return;
+        }
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            first_error.store(MBL_ERR_CUDA);
+            return;
+        }
+        cudaStreamWaitEvent(st, start_ev, 0);
+        void *ws = (char *)workspace_dev + slot * (size_t)wid;
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nprob || first_error.load() != MBL_OK) break;
+            const mbl_chain &ch = chains[i];
+            mbl_lobpcg_opts o = *opts;
+            double sigma = sigmas ? sigmas[i] : 0.0;
+            if (!sigmas) {
+                // sigma at the middle of the spectrum; ||H|| from the same bounds
+                double lo = 0.0, hi = 0.0;
+                int it = 0;
+                const double *xb = X0_dev + off_x[i];
+                int r1 = bounds_one(&ch, kBatchBoundsK, kBatchBoundsTol, 1000, xb, opts->k, ws, slot, 0, &lo, &it, st);
+                int r2 = (r1 == MBL_OK || r1 == MBL_ERR_NOT_CONVERGED)
+                             ? bounds_one(&ch, kBatchBoundsK, kBatchBoundsTol, 1000, xb, opts->k, ws, slot, 1, &hi,
+                                          &it, st)
+                             : r1;
+                if ((r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) || (r2 != MBL_OK && r2 != MBL_ERR_NOT_CONVERGED)) {
+                    first_error.store(r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED ? r1 : r2);
+                    break;
+                }
+                sigma = 0.5 * (lo + hi);
+                if (!(o.norm_h > 0.0)) o.norm_h = std::max(std::fabs(lo), std::fabs(hi));
+            }
+            mbl_lobpcg_stats stt{};
+            const int r = mbl_lobpcg_solve(&ch, sigma, &o, X0_dev + off_x[i], ws, slot,
+                                           evals_host ? evals_host + (size_t)i * o.nev : nullptr,
+                                           evecs_dev ? evecs_dev + off_v[i] : nullptr,
+                                           resid_host ? resid_host + (size_t)i * o.nev : nullptr, &stt,
+                                           (mbl_stream_t)st);
+            if (stats) stats[i] = stt;
+            if (r == MBL_ERR_NOT_CONVERGED) {
+                not_converged.fetch_add(1);
+            } else if (r != MBL_OK) {
+                int expect = MBL_OK;
+                first_error.compare_exchange_strong(expect, r);
+                break;
+            }
+        }
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(ns);
+    for (int w = 0; w < ns; ++w) pool.emplace_back(worker, w);
+    for (auto &t : pool) t.join();
+    cudaEventDestroy(start_ev);
+    if (first_error.load() != MBL_OK) return first_error.load();
+    return not_converged.load() ? MBL_ERR_NOT_CONVERGED : MBL_OK;
 }

@@ -235,11 +235,11 @@ size_t small_eig_work_doubles(int n) { return (size_t)2 * n * pad_ld(n) + 8; }
 
 int small_eig(int n, const double *G, int64_t ldg, double *w, double *Z, double *work, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr_once = [&]() {
         cudaFuncSetAttribute(k_small_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_smem_bytes(64));
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr_once;
     const int in_smem = n <= 64;
     k_small_eig<<<1, kSmallThreads, in_smem ? eig_smem_bytes(n) : 0, st>>>(n, G, ldg, w, Z, work, in_smem);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
@@ -437,13 +437,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_rr(int w, int k, int la
 int small_svqb_rr(int w, int k, int largest, int mixed, const double *GS, const double *GA, double tau,
                   double *coef, double *theta, double *work, int *info, cudaStream_t st)
 {
-    static bool attr = false;
     const int cap = 160 * 1024;
-    if (!attr) {
+    static const bool attr_once = [&]() {
         cudaFuncSetAttribute(k_small_rr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
         cudaFuncSetAttribute(k_small_rr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr_once;
     const size_t es = mixed ? sizeof(float) : sizeof(double);
     const size_t sm = 2 * (size_t)w * pad_ld(w) * es;
     const int use_smem = sm <= (size_t)cap;
