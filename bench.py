@@ -9,9 +9,14 @@ Metric: eigenpairs per second.  Also reported: the same solve in plain FP64, the
 block-product bandwidth sweep on L = 22..28 open chains (the roofline), the e2e
 figure through the C ABI with host buffers, and the CPU oracle on a bounded sample.
 
+Multi-GPU (torchrun, one rank per GPU): weak scaling over disorder realisations -- rank
+r solves the same workload with field seed 1 + 1000 r; no data-path collective, only the
+max over ranks of the timed region.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -32,6 +37,56 @@ L2_FLUSH_BYTES = 512 << 20
 # Residual tolerance of the extreme Ritz pairs: their eigenvalues are then accurate to
 # about tol^2 |E| / gap, far below what sigma and ||H|| need.
 BOUNDS_TOL = 1e-7
+
+
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "product_kernel_l20_l26.md")
+PRODUCT_SOURCE = os.path.join(ROOT, "paper_2012_00217_gb300", "csrc", "mbl_apply.cu")
+BATCH_SAMPLE = dict(W=(2.0, 4.0, 8.0), per_w=dict(L16=10, L14=3, L18=3), nev=8, k=16, pcg_iters=80)
+
+
+def rank_env():
+    """(world size, rank, local rank) from the torchrun environment (1, 0, 0 without)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(seed, rank):
+    """Field seed of rank r: independent disorder realisations (weak scaling); rank 0
+    keeps the workload's own seed."""
+    return int(seed) + 1000 * int(rank)
+
+
+def reduce_max(x, dist=None, device="cpu"):
+    """Max of a float over ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput: units processed by all ranks / the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
+def profiled_traffic(key):
+    """DRAM bytes per launch of a product kernel from the committed ncu summary, or None
+    when the summary is absent or the kernel source has changed since it was taken."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        sha = hashlib.sha1(open(PRODUCT_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    src, val = None, None
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        if line.startswith("source_sha1:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch[%s]:" % key):
+            val = float(line.split(":", 1)[1].strip())
+    return val if (src == sha and val is not None) else None
 
 
 def _peaks():
@@ -89,14 +144,15 @@ class Clocks:
         return out
 
 
-def _setup(torch, mbl, dev):
+def _setup(torch, mbl, dev, seed=None):
     L, k, nev = CFG["L"], CFG["k"], CFG["nev"]
-    h = wl.fields(L, CFG["W"], CFG["seed"])
+    seed = CFG["seed"] if seed is None else seed
+    h = wl.fields(L, CFG["W"], seed)
     n = mbl.basis_size(L, L // 2)
     chain = mbl.make_chain(L, h, CFG["delta"], CFG["periodic"])
-    X0_host = torch.from_numpy(wl.initial_block(n, k, CFG["seed"])).pin_memory()
-    Xb_host = torch.from_numpy(wl.block(n, 4, CFG["seed"] + 100)).pin_memory()
-    return dict(L=L, k=k, nev=nev, h=h, n=n, chain=chain, X0_host=X0_host, Xb_host=Xb_host)
+    X0_host = torch.from_numpy(wl.initial_block(n, k, seed)).pin_memory()
+    Xb_host = torch.from_numpy(wl.block(n, 4, seed + 100)).pin_memory()
+    return dict(L=L, k=k, nev=nev, h=h, n=n, chain=chain, X0_host=X0_host, Xb_host=Xb_host, seed=seed)
 
 
 class Step:
@@ -218,9 +274,11 @@ def matvec_roofline(torch, mbl, dev, peak_gbs, quick=False):
 
 
 def solve_kernel_roofline(torch, mbl, dev, s, peak_gbs):
-    """The dominant kernel of the step: the FP32 block product of every PCG step
-    (n = 184,756, k = 32).  Timed alone with CUDA events over a replayed graph: back to
-    back as in the solve (its 47 MB of operands stay in L2) and with L2 flushed."""
+    """The dominant kernel of the step: the FP32 tiled block product that every PCG step
+    launches twice (n = 184,756, k = 32; the PCG launches add only an epilogue of
+    per-column dot products).  Timed with CUDA events on its launching stream over a
+    replayed graph: back to back as in the solve (its 47 MB of operands stay in L2) and
+    with L2 flushed before each launch."""
     chain, n, k = s["chain"], s["n"], s["k"]
     g = torch.Generator(device=dev)
     g.manual_seed(5)
@@ -231,8 +289,38 @@ def solve_kernel_roofline(torch, mbl, dev, s, peak_gbs):
     t_warm = _graph_time(torch, fn, 50)
     t_cold = _graph_time(torch, fn, 20, flush)
     alg = 2.0 * n * k * 4
-    return dict(kernel="k_apply<float,32> (PCG block product)", alg_bytes=alg, t_l2_warm_us=t_warm * 1e6,
+    return dict(kernel="k_apply_tiled<float,32> (PCG block product)", alg_bytes=alg, t_l2_warm_us=t_warm * 1e6,
                 t_cold_us=t_cold * 1e6, gbs_cold=alg / t_cold / 1e9, gbs_warm=alg / t_warm / 1e9)
+
+
+def batched_sample(torch, mbl, dev, nstreams=16):
+    """Disorder averaging (uneven L, several W): a bounded sample of the 352-problem
+    batch -- per W in {2, 4, 8}: 10 x L=16, 3 x L=14, 3 x L=18 (the first seeds of each
+    group) -- 8 mid-spectrum eigenpairs each (sigma from each problem's own spectrum
+    bounds), mixed precision, one call.  Returns eigenpairs/s over the whole call."""
+    probs = wl.batched_problems(1.0)
+    pick = probs[:BATCH_SAMPLE["per_w"]["L16"]] + probs[256:256 + BATCH_SAMPLE["per_w"]["L14"]] + \
+        probs[320:320 + BATCH_SAMPLE["per_w"]["L18"]]
+    chains, X0s = [], []
+    k, nev = BATCH_SAMPLE["k"], BATCH_SAMPLE["nev"]
+    for W in BATCH_SAMPLE["W"]:
+        for p in pick:
+            chains.append(mbl.make_chain(p["L"], wl.batched_fields(p["L"], W, p["seed"]), p["delta"], p["periodic"]))
+            X0s.append(torch.from_numpy(wl.initial_block(wl.sector_dim(p["L"]), k, p["seed"])))
+    X0 = torch.cat(X0s).to(dev)
+    opts = mbl.make_opts(nev, k, tol=1e-8, max_iter=1000, pcg_iters=BATCH_SAMPLE["pcg_iters"], mode=mbl.MODE_MIXED)
+    ws = torch.empty(mbl.binding.batched_workspace_size(chains, opts, nstreams), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    # the batched call returns when every problem is done (its worker streams are
+    # synchronised), so the host clock around it is the call's time
+    t0 = time.perf_counter()
+    ev, res, stats, rc = mbl.binding.lobpcg_solve_batched(chains, opts, X0, ws, nstreams)
+    t = time.perf_counter() - t0
+    its = [st["iters"] for st in stats]
+    return dict(value=len(chains) * nev / t, unit="eigenpairs/s", seconds=t, problems=len(chains), nev=nev, k=k,
+                streams=nstreams, pcg_iters=BATCH_SAMPLE["pcg_iters"], iters_mean=float(np.mean(its)),
+                iters_max=int(max(its)), max_rel_resid=float(max(st["max_rel_resid"] for st in stats)),
+                sample="per W in {2,4,8}: seeds 0-9 (L=16), 256-258 (L=14), 320-322 (L=18), open chains")
 
 
 def cpu_baseline(s, gpu_iters, budget_s=20.0):
@@ -331,7 +419,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--quick", action="store_true", help="skip the sweep and the CPU baseline")
+    ap.add_argument("--quick", action="store_true", help="skip the sweep, the batch and the CPU baseline")
     ap.add_argument("--profile", choices=["product", "pcg", "bounds"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
                          "FP32) or a 3-iteration solve, for an ncu capture")
@@ -344,9 +432,8 @@ def main():
     import torch
     import paper_2012_00217_gb300 as mbl
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
+    dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -355,30 +442,35 @@ def main():
     mbl.binding.lib()
     peaks, peak_kind = _peaks()
 
-    s = _setup(torch, mbl, dev)
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    s = _setup(torch, mbl, dev, rank_seed(CFG["seed"], rank))
     step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         step.run()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier()
     clocks = Clocks()
     clocks.start()
+    launches0 = mbl.binding.kernel_launch_count()
     times = _time_steps(torch, step.run, args.steps, flush)
+    launches = mbl.binding.kernel_launch_count() - launches0
+    barrier()
     ck = clocks.stop()
-    t_step = float(np.max(times))
-    t_med = float(np.median(times))
-    if world > 1:
-        tt = torch.tensor([t_med], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_med = float(tt.item())
+    t_total = reduce_max(float(np.sum(times)), dist, dev)
     res = step.last
-    value = world * s["nev"] / t_med
+    value = whole_job_rate(s["nev"] * args.steps, world, t_total)
     # e2e through the ABI with host buffers
     evecs_host = torch.empty((s["n"], s["nev"]), dtype=torch.float64).pin_memory()
-    e2e_times = _time_steps(torch, lambda: step.run_e2e(s["X0_host"], s["Xb_host"], evecs_host),
-                            max(2, args.steps // 2), flush)
+    ke = max(2, args.steps // 2)
+    barrier()
+    e2e_times = _time_steps(torch, lambda: step.run_e2e(s["X0_host"], s["Xb_host"], evecs_host), ke, flush)
+    barrier()
+    e2e_total = reduce_max(float(np.sum(e2e_times)), dist, dev)
     h2d = s["X0_host"].numel() * 8 + s["Xb_host"].numel() * 8
     d2h = evecs_host.numel() * 8 + 2 * s["nev"] * 8
     # plain FP64 solve for comparison
@@ -398,6 +490,7 @@ def main():
     sweep = [] if args.quick else matvec_roofline(torch, mbl, dev, peaks["hbm_gbs"])
     big = [r for r in sweep if r["L"] == 26 and r["k"] == 64 and r["dtype"] == "f32"]
     head = big[0] if big else None
+    batch = None if args.quick else batched_sample(torch, mbl, dev)
 
     line = {
         "metric": METRIC,
@@ -406,7 +499,7 @@ def main():
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": t_med * 1e3,
+        "ms_per_step": t_total / args.steps * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -414,7 +507,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": CFG["name"], "L": s["L"], "n": s["n"], "nev": s["nev"], "k": s["k"],
                    "pcg_iters": PCG_ITERS, "tol": 1e-8, "mode": "mixed", "l2": "flushed between steps",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "weak: rank r field seed %d + 1000 r" % CFG["seed"] if world > 1 else "single"},
         "solve": {"iters": res["stats"]["iters"], "matvecs": res["stats"]["matvecs"],
                   "max_rel_resid": res["stats"]["max_rel_resid"], "sigma": res["sigma"],
                   "emin": res["emin"], "emax": res["emax"], "bounds_iters": res["bounds_iters"],
@@ -423,27 +516,34 @@ def main():
                  "max_rel_resid": res64["stats"]["max_rel_resid"],
                  "max_eval_diff_vs_mixed_rel": float(np.max(np.abs(res64["evals"] - res["evals"])) /
                                                      res["stats"]["norm_h"])},
-        "e2e": {"value": world * s["nev"] / float(np.median(e2e_times)), "unit": "eigenpairs/s",
+        "e2e": {"value": whole_job_rate(s["nev"] * ke, world, e2e_total), "unit": "eigenpairs/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": None,
-        "roofline": None,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": kern["gbs_warm"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": kern["gbs_warm"] / peaks["hbm_gbs"],
+                     "traffic": profiled_traffic("L20_k32_f32"),
+                     "kernel": kern["kernel"] + ", algorithmic 2nk*4 B per launch / CUDA-event launch time",
+                     "peak_kind": peak_kind + " (hbm_gbs)"},
+        "matvec_roofline": None,
         "solve_kernel": kern,
         "solve_phases_s": phases,
         "bounds_s": t_b,
+        "batched": batch,
         "matvec_sweep": sweep,
         "clocks": ck,
     }
     if head is not None:
-        line["roofline"] = {"bound": "hbm", "achieved": head["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                            "frac": head["gbs"] / peaks["hbm_gbs"], "traffic": None,
-                            "kernel": "k_apply<float,64> L=26 open k=64 (block product)",
-                            "peak_kind": peak_kind + " (hbm_gbs)"}
+        line["matvec_roofline"] = {"bound": "hbm", "achieved": head["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": head["gbs"] / peaks["hbm_gbs"],
+                                   "traffic": profiled_traffic("L26_k64_f32"),
+                                   "kernel": "k_apply_tiled<float,64> L=26 open k=64 (block product), L2 flushed",
+                                   "peak_kind": peak_kind + " (hbm_gbs)"}
     if rank == 0 and world == 1 and not args.quick:
         line["cpu_baseline"] = cpu_baseline(s, res["stats"]["iters"])
     if rank == 0:
         print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

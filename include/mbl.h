@@ -57,6 +57,12 @@ typedef struct CUstream_st *mbl_stream_t; /* identical to cudaStream_t */
 /* Human-readable text for a status code (static storage). */
 const char *mbl_status_string(int status);
 
+/* Number of GPU kernels this library has launched in the calling process since it was
+ * loaded, over all threads and devices: each direct launch counts one, each replay of a
+ * captured CUDA graph counts its kernel nodes.  Monotone; for instrumentation (the
+ * difference of two readings is the launches in between).  Never fails. */
+int64_t mbl_kernel_launch_count(void);
+
 /* One disorder realisation of the chain.  h_host: L FP64 fields (host memory, read
  * during the call only).  Requirements: 2 <= L <= 32, 0 <= n_up <= L, finite h and
  * delta. */
@@ -96,18 +102,29 @@ int mbl_hamiltonian_apply(const mbl_chain *chain, double sigma, int dtype, const
                           mbl_stream_t stream);
 
 /* Tuning: the product kernels split a state into B low bits and L - B high bits; all
- * states with the same high bits form one tile of consecutive rows, staged in shared
- * memory, and high-bond neighbours are whole tiles at the same in-tile offsets.  This
- * sets B for products of block width k and type dtype in this process: 0 = built-in
- * heuristic (default), -1 = untiled kernel, 2..16 = that B (capped at L - 1, and
- * lowered until the largest tile fits in shared memory).  Results
- * differ only in the order of floating-point additions.  Not thread-safe against
- * concurrent products. */
+ * states with the same high bits form one tile of consecutive rows, in-tile neighbours
+ * come from a per-B table of low patterns, and high-bond neighbours are whole tiles at
+ * the same in-tile offsets.  This sets B for products of block width k and type dtype
+ * in this process: 0 = built-in heuristic (default), -1 = untiled kernel, 2..16 = that
+ * B (capped at 13 and at L - 2).  Results differ only in the order of floating-point
+ * additions.  Returns MBL_ERR_ARG for k outside 1..256, an unknown dtype or bits
+ * outside {-1, 0, 2..16}.  Not thread-safe against concurrent products. */
 int mbl_set_product_tile_bits(int k, int dtype, int bits);
 
 /* Tuning: bytes of each row that one lane moves per neighbour in the tiled product
- * (16 or 32; 0 = default 32) for block width k and type dtype. */
+ * (16 or 32; 0 = default 32) for block width k and type dtype.  Returns MBL_ERR_ARG
+ * for any other value, k outside 1..256 or an unknown dtype. */
 int mbl_set_product_lane_bytes(int k, int dtype, int bytes);
+
+/* Tuning: work order of the plain tiled product (mbl_hamiltonian_apply and the FP64
+ * products inside the solver) for block width k and type dtype.  0 = by size (default:
+ * ordered for rows of k * element size >= 256 bytes once C(L, n_up) * k * element size
+ * reaches 1 GiB in FP32 or 128 MiB in FP64), 1 = persistent (a few blocks
+ * per SM striding over the tiles), 2 = ordered (one 32-row chunk per warp; the
+ * hardware dispatches blocks in index order, so the tiles being read advance as a
+ * narrow window that stays in L2).  Results are bitwise identical under every order.
+ * Returns MBL_ERR_ARG for schedule outside 0..2, k outside 1..256 or an unknown dtype. */
+int mbl_set_product_schedule(int k, int dtype, int schedule);
 
 /* ---- folded-spectrum LOBPCG (Sec. 3.2, Sec. 6.2) ---------------------------------- */
 

@@ -32,7 +32,8 @@ EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis
             "mbl_hamiltonian_apply", "mbl_lobpcg_workspace_size", "mbl_lobpcg_solve",
             "mbl_bounds_workspace_size", "mbl_spectrum_bounds", "mbl_lobpcg_solve_noalloc",
             "mbl_set_product_tile_bits", "mbl_set_product_lane_bytes", "mbl_batched_workspace_size",
-            "mbl_lobpcg_solve_batched")
+            "mbl_lobpcg_solve_batched", "mbl_kernel_launch_count",
+            "mbl_set_product_schedule")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -76,6 +77,8 @@ def lib():
     popt = ctypes.POINTER(LobpcgOpts)
     so.mbl_status_string.restype = ctypes.c_char_p
     so.mbl_status_string.argtypes = [i32]
+    so.mbl_kernel_launch_count.restype = i64
+    so.mbl_kernel_launch_count.argtypes = []
     so.mbl_basis_size.restype = i64
     so.mbl_basis_size.argtypes = [i32, i32]
     so.mbl_basis_build.restype = i32
@@ -91,6 +94,8 @@ def lib():
                                             ctypes.POINTER(LobpcgStats), p]
     so.mbl_set_product_lane_bytes.restype = i32
     so.mbl_set_product_lane_bytes.argtypes = [i32, i32, i32]
+    so.mbl_set_product_schedule.restype = i32
+    so.mbl_set_product_schedule.argtypes = [i32, i32, i32]
     so.mbl_set_product_tile_bits.restype = i32
     so.mbl_set_product_tile_bits.argtypes = [i32, i32, i32]
     so.mbl_lobpcg_workspace_size.restype = i32
@@ -108,6 +113,12 @@ def lib():
 
 def status_string(status):
     return lib().mbl_status_string(int(status)).decode()
+
+
+def kernel_launch_count():
+    """Kernels the library has launched in this process (graph replays count their
+    kernel nodes)."""
+    return int(lib().mbl_kernel_launch_count())
 
 
 def _check(rc, what, ok=(MBL_OK,)):
@@ -200,6 +211,13 @@ def set_product_lane_bytes(k, dtype, nbytes):
     torch = _torch()
     dt = MBL_F32 if dtype == torch.float32 else MBL_F64
     _check(lib().mbl_set_product_lane_bytes(int(k), dt, int(nbytes)), "mbl_set_product_lane_bytes")
+
+
+def set_product_schedule(k, dtype, schedule):
+    """mbl_set_product_schedule: 0 by size, 1 persistent, 2 ordered."""
+    torch = _torch()
+    dt = MBL_F32 if dtype == torch.float32 else MBL_F64
+    _check(lib().mbl_set_product_schedule(int(k), dt, int(schedule)), "mbl_set_product_schedule")
 
 
 def make_opts(nev, k, tol=1e-8, max_iter=200, pcg_iters=50, pcg_tol=0.0, norm_h=0.0,

@@ -46,6 +46,10 @@ struct WideRowLayout {
     static constexpr int V = kBytes >= LB ? LB / (int)sizeof(T) : (kBytes >= 16 ? 16 / (int)sizeof(T) : K);
     static constexpr int G = K / V;
     static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
+    // rows per work item of the tiled product: at least four row-passes of the warp
+    // (32 / G rows each) and at least 32 rows, so the per-tile setup of an item (tile
+    // offset, high-bond shifts) is spread over enough rows
+    static constexpr int CH = (4 * (32 / G) > 32) ? 4 * (32 / G) : 32;
 };
 
 constexpr int kThreads = 256;
@@ -102,6 +106,21 @@ template <typename T, int V>
 __device__ __forceinline__ void stv(T *p, const Vec<T, V> &x)
 {
     *reinterpret_cast<Vec<T, V> *>(p) = x;
+}
+
+// Store with the evict-first hint: a product's output is not read again by the same
+// launch, so it should not push the input's rows out of L2.
+template <typename T, int V>
+__device__ __forceinline__ void stv_stream(T *p, const Vec<T, V> &x)
+{
+    if constexpr ((V * sizeof(T)) % 16 == 0) {
+        const float4 *src = reinterpret_cast<const float4 *>(&x);
+        float4 *dst = reinterpret_cast<float4 *>(p);
+#pragma unroll
+        for (int i = 0; i < (int)(V * sizeof(T) / 16); ++i) __stcs(dst + i, src[i]);
+    } else {
+        stv<T, V>(p, x);
+    }
 }
 
 // Gather the neighbour rows listed in nbl[0..f) into acc: chunks of 8 independent
@@ -167,7 +186,10 @@ __device__ __forceinline__ void finish_row(const T (&acc)[V], int f, uint32_t r,
         Vec<T, V> y;
 #pragma unroll
         for (int v = 0; v < V; ++v) y.v[v] = acc[v];
-        stv<T, V>(Y + (int64_t)r * ldy + col, y);
+        if (MODE == 0)
+            stv_stream<T, V>(Y + (int64_t)r * ldy + col, y);
+        else
+            stv<T, V>(Y + (int64_t)r * ldy + col, y);
         if (MODE == 1) {
 #pragma unroll
             for (int v = 0; v < V; ++v) part[v] += acc[v] * acc[v];
@@ -408,7 +430,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(ChainParams cp, const T *__r
 //   * the wrap bond of a periodic chain: rank = offset of tile t ^ 2^(H-1) plus the rank
 //     of u ^ 1 in its class.
 // Everything that depends on the low pattern alone comes from a small table built once
-// per tile width (LowRec); each warp processes 32 rows of one tile.
+// per tile width (LowRec); each warp processes a chunk of rows of one tile.
 
 constexpr uint32_t kNoRow = 0xffffffffu;
 
@@ -429,14 +451,38 @@ static __device__ LowRec g_lowtab[kLowRecords];
 
 __host__ __device__ inline int lowtab_base(int B) { return (1 << B) - 4; }
 
+// Resident blocks per SM the tiled kernel is compiled for (register budget 65536 /
+// (256 * this)); 3 keeps every variant free of spills.
+#ifndef MBL_TILED_MIN_BLOCKS
+#define MBL_TILED_MIN_BLOCKS 3
+#endif
+
 template <typename T, int K, int MODE, int LB>
-__global__ void __launch_bounds__(kThreads, 3) k_apply_tiled(ChainParams cp, int B, const T *__restrict__ X,
+__global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(ChainParams cp, int B, const T *__restrict__ X,
                                                           int64_t ldx, T *__restrict__ Y, int64_t ldy,
                                                           T *__restrict__ R, const T *__restrict__ dinv,
                                                           PcgScalars ps, Reduce rd)
 {
     using Lay = WideRowLayout<T, K, LB>;
-    constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G, CH = 32;
+    constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G, CH = Lay::CH;
+    if (MODE == kPlain) {
+        // ordered schedule (at most one item per warp): a block whose items hold no rows
+        // leaves before any setup
+        const uint32_t nch = (c_binom.v[B * kBinomDim + B / 2] + CH - 1) / CH;
+        const uint32_t tot = (1u << (cp.L - B)) * nch;
+        if ((uint64_t)gridDim.x * kWarps >= tot) {
+            int any = 0;
+            if (threadIdx.x < kWarps) {
+                const uint32_t item = blockIdx.x * kWarps + threadIdx.x;
+                if (item < tot) {
+                    const uint32_t t = item / nch, c = item % nch;
+                    const int p = cp.n_up - __popc(t);
+                    any = (p >= 0 && p <= B && c * CH < c_binom.v[B * kBinomDim + p]) ? 1 : 0;
+                }
+            }
+            if (!__syncthreads_or(any)) return;
+        }
+    }
     __shared__ uint32_t sbin[kBinomDim * kBinomDim];
     __shared__ T tab[1024];
     __shared__ T red[kWarps][64];
@@ -469,7 +515,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply_tiled(ChainParams cp, int
     }
     const uint32_t gw = blockIdx.x * kWarps + (threadIdx.x >> 5), nw = gridDim.x * kWarps;
     for (uint32_t item = gw; item < total; item += nw) {
-        const uint32_t t = item % ntile, c = item / ntile;
+        // tile-major: the warps in flight cover a run of consecutive tiles, so in-tile
+        // neighbours and the tiles reached by the low high-part bonds stay in L2
+        const uint32_t t = item / nchunk, c = item % nchunk;
         const int p = m - __popc(t);
         if (p < 0 || p > B) continue;  // warp-uniform
         const uint32_t Rt = binom(sbin, B, p);
@@ -552,15 +600,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply_tiled(ChainParams cp, int
                 }
                 if (join) a = ldv<T, V>(xr + (ub ? (int64_t)sup : -(int64_t)sdn) * ldx);
                 if (wrap) b = ldv<T, V>(X + (int64_t)(offper + (w0.y & 0xffffu)) * ldx + col);
+                if (cp.periodic) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] += half * (a.v[v] + b.v[v]);
+                    for (int v = 0; v < V; ++v) acc[v] += half * (a.v[v] + b.v[v]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] += half * a.v[v];
+                }
             }
-            // low-part neighbours, in-tile ranks unpacked from the record
+            // low-part neighbours, in-tile ranks unpacked from the record; adds stop at the
+            // warp's largest count (no arithmetic on padding: FP64 is ALU-bound here)
             {
                 const uint32_t nbw[6] = {w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                const int cmax = (int)__reduce_max_sync(0xffffffffu, valid ? cnt : 0u);
 #pragma unroll
                 for (int q0 = 0; q0 < 12; q0 += 4) {
-                    if (q0 >= (int)cnt) break;
+                    if (q0 >= cmax) break;
                     Vec<T, V> a[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
@@ -572,19 +627,26 @@ __global__ void __launch_bounds__(kThreads, 3) k_apply_tiled(ChainParams cp, int
                     }
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
+                        if (q0 + e < cmax)
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] += half * a[e].v[v];
+                            for (int v = 0; v < V; ++v) acc[v] += half * a[e].v[v];
                 }
             }
-            // high-part neighbours: the same shift for the whole tile
-#pragma unroll 4
-            for (int hh = 0; hh < nh; ++hh) {
-                const uint32_t sh = __shfl_sync(0xffffffffu, hshift, hh);
-                if (valid) {
-                    const Vec<T, V> a = ldv<T, V>(xr + (int64_t)(int32_t)sh * ldx);
+            // high-part neighbours: the same shift for the whole tile, four loads in flight
+            for (int h0 = 0; h0 < nh; h0 += 4) {
+                Vec<T, V> a[4];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] += half * a.v[v];
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t sh = __shfl_sync(0xffffffffu, hshift, (h0 + e) & 31);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
+                    if (valid && h0 + e < nh) a[e] = ldv<T, V>(xr + (int64_t)(int32_t)sh * ldx);
                 }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (h0 + e < nh)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] += half * a[e].v[v];
             }
             if (valid) finish_row<T, V, MODE>(acc, 0, r, Y, ldy, R, dinv, col, alpha, part);
         }
@@ -1001,6 +1063,7 @@ static cudaError_t launch_apply_k(const ChainParams &cp, const T *X, int64_t ldx
         return true;
     }();
     (void)attr_set_once;
+    note_launch();
     kern<<<grid, kThreads, sm, st>>>(cp, X, ldx, Y, ldy, n, R, dinv, ps, rd);
     return cudaGetLastError();
 }
@@ -1011,6 +1074,7 @@ static cudaError_t launch_apply_k(const ChainParams &cp, const T *X, int64_t ldx
 // >= 2 = that many low bits.  Set by the autotuner.
 static int g_tile_bits[2][8] = {};
 static int g_lane_bytes[2][8] = {};  // 0: default (32), else 16 or 32
+static int g_schedule[2][8] = {};    // 0: by size, 1: persistent grid-stride, 2: ordered
 
 static int kslot(int K)
 {
@@ -1059,6 +1123,25 @@ int tile_bits_for(int L, int K, size_t es)
 
 void set_tile_bits(int K, size_t es, int bits) { g_tile_bits[es == 8 ? 1 : 0][kslot(K)] = bits; }
 void set_lane_bytes(int K, size_t es, int bytes) { g_lane_bytes[es == 8 ? 1 : 0][kslot(K)] = bytes; }
+void set_schedule(int K, size_t es, int mode) { g_schedule[es == 8 ? 1 : 0][kslot(K)] = mode; }
+
+// Work order of a plain tiled product.  Persistent: a grid of a few blocks per SM, each
+// warp striding over the (tile, chunk) items.  Ordered: one item per warp and as many
+// blocks as needed, so the hardware hands out blocks in index order and the tiles in
+// flight stay a narrow, advancing window; with the grid-stride loop, warps that meet
+// many empty chunks run ahead and the window widens beyond L2.  Every block of the
+// ordered grid repeats the shared-memory setup, so it only pays for wide rows: measured
+// on GB300, ordered wins for rows of >= 256 bytes once the block vector is >= 1 GiB
+// (FP32), or >= 128 MiB in FP64 (ALU-bound there), and loses elsewhere.
+static bool ordered_schedule(int L, int n_up, int K, size_t es)
+{
+    const int o = g_schedule[es == 8 ? 1 : 0][kslot(K)];
+    if (o == 1) return false;
+    if (o == 2) return true;
+    const double bytes = (double)host_binom(L, n_up) * K * (double)es;
+    if (K * (int)es < 256) return false;
+    return bytes >= (es == 8 ? 128.0 * (1 << 20) : 1024.0 * (1 << 20));
+}
 static int lane_bytes_for(int K, size_t es)
 {
     const int v = g_lane_bytes[es == 8 ? 1 : 0][kslot(K)];
@@ -1078,10 +1161,15 @@ static cudaError_t launch_tiled_lb(const ChainParams &cp, int B, const T *X, int
         return v;
     }();
     const uint32_t rmax = host_binom(B, B / 2);
-    const int64_t items = ((int64_t)1 << (cp.L - B)) * (int64_t)((rmax + 31) / 32);
+    constexpr int CH = WideRowLayout<T, K, LB>::CH;
+    const int64_t items = ((int64_t)1 << (cp.L - B)) * (int64_t)((rmax + CH - 1) / CH);
     int64_t grid = (int64_t)num_sms() * per_sm;
     if (grid > (int64_t)num_sms() * 8) grid = (int64_t)num_sms() * 8;  // partials capacity
     const int64_t need = (items + kWarps - 1) / kWarps;
+    // the ordered schedule (one item per warp) only for the plain product: the PCG
+    // epilogues keep one partial per block in a buffer sized for the persistent grid
+    if (MODE == kPlain && ordered_schedule(cp.L, cp.n_up, K, sizeof(T))) grid = need;
+    note_launch();
     if (grid > need) grid = need;
     kern<<<(int)grid, kThreads, 0, st>>>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd);
     return cudaGetLastError();
@@ -1163,6 +1251,7 @@ static int dispatch_plain(const ChainParams &cp, const T *X, int64_t ldx, T *Y, 
             return true;
         }();
         (void)attr_set_once;
+        note_launch();
         k_apply_generic<T><<<grid, kThreads, sm, st>>>(cp, X, ldx, Y, ldy, n, k);
         e = cudaGetLastError();
     }
@@ -1181,6 +1270,7 @@ template <typename T>
 int pcg_fold_dinv(const ChainParams &cp, uint32_t n, T *dinv, cudaStream_t st)
 {
     int grid = (int)(((int64_t)n + kThreads - 1) / kThreads);
+    note_launch();
     if (grid > num_sms() * 8) grid = num_sms() * 8;
     k_fold_dinv<T><<<grid, kThreads, 0, st>>>(cp, n, dinv);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
@@ -1194,6 +1284,7 @@ int gershgorin_bound(const ChainParams &cp, uint32_t n, double *partials, unsign
     int grid = (int)(((int64_t)n + kThreads - 1) / kThreads);
     if (grid > num_sms() * 4) grid = num_sms() * 4;
     Reduce rd{partials, counter};
+    note_launch();
     k_gershgorin<<<grid, kThreads, 0, st>>>(cp, n, rd, out);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -1208,6 +1299,7 @@ int pcg_start(const double *B, int64_t ldb, const double *bnorm, uint32_t n, int
     PcgScalars ps{pd.rz, pd.rz0, pd.alpha, pd.beta, pd.active, pd.tol2};
     Reduce rd{pd.partials, pd.counter};
     int grid = pcg_grid(n);
+    note_launch();
     k_pcg_init<T><<<grid, kThreads, 0, st>>>(B, ldb, bnorm, n, k, dinv, r, p, w, ps, rd);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -1233,6 +1325,7 @@ static cudaError_t pcg_step_k(const ChainParams &cp, uint32_t n, const T *dinv, 
     }
     if (e != cudaSuccess) return e;
     int ugrid = (int)(((int64_t)n * RowLayout<T, K>::G + kThreads - 1) / kThreads);
+    note_launch();
     if (ugrid > num_sms() * 8) ugrid = num_sms() * 8;
     k_pcg_update<T, K><<<ugrid, kThreads, 0, st>>>(n, dinv, r, p, w, ps);
     return cudaGetLastError();
@@ -1261,9 +1354,12 @@ int pcg_step(const ChainParams &cp, uint32_t n, int k, const T *dinv, T *r, T *p
             return true;
         }();
         (void)attr_set_once;
+        note_launch();
         k_apply_pcg_generic<T, kPcgT><<<grid, kThreads, sm, st>>>(cp, p, t, n, k, nullptr, dinv, ps, rd);
+        note_launch();
         k_apply_pcg_generic<T, kPcgQ><<<grid, kThreads, sm, st>>>(cp, t, nullptr, n, k, r, dinv, ps, rd);
         int ugrid = num_sms() * 8;
+        note_launch();
         k_pcg_update_generic<T><<<ugrid, kThreads, 0, st>>>(n, k, dinv, r, p, w, ps);
         e = cudaGetLastError();
     }
@@ -1285,6 +1381,14 @@ extern "C" int mbl_set_product_tile_bits(int k, int dtype, int bits)
     if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || bits < -1 || bits > 16 || bits == 1)
         return MBL_ERR_ARG;
     mbl::set_tile_bits(k, dtype == MBL_F32 ? 4 : 8, bits);
+    return MBL_OK;
+}
+
+extern "C" int mbl_set_product_schedule(int k, int dtype, int schedule)
+{
+    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || schedule < 0 || schedule > 2)
+        return MBL_ERR_ARG;
+    mbl::set_schedule(k, dtype == MBL_F32 ? 4 : 8, schedule);
     return MBL_OK;
 }
 

@@ -58,6 +58,7 @@ extern "C" int mbl_basis_build(int L, int n_up, uint32_t *states_dev, int64_t n,
     const uint32_t run = 16;
     const int64_t threads = (n + run - 1) / run;
     const int grid = (int)((threads + 255) / 256);
+    mbl::note_launch();
     mbl::k_basis_build<<<grid, 256, 0, (cudaStream_t)stream>>>(L, n_up, (uint32_t)n, run, states_dev);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -70,6 +71,7 @@ extern "C" int mbl_basis_rank(int L, int n_up, const uint32_t *words_dev, int64_
     if (!words_dev || !ranks_dev) return MBL_ERR_ARG;
     int64_t blocks = (cnt + 255) / 256;
     const int64_t cap = (int64_t)mbl::num_sms() * 16;
+    mbl::note_launch();
     mbl::k_basis_rank<<<(int)(blocks < cap ? blocks : cap), 256, 0, (cudaStream_t)stream>>>(L, n_up, words_dev,
                                                                                           ranks_dev, cnt);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;

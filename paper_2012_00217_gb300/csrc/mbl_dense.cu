@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include "mbl_dense.h"
+#include "mbl_internal.h"
 
 namespace mbl {
 
@@ -121,6 +122,7 @@ static void launch_gram(const double *A, int64_t lda, int p, const double *B, in
                         int64_t rps, int nslab, double *part, cudaStream_t st)
 {
     dim3 grid((p + TS - 1) / TS, (q + TS - 1) / TS, nslab);
+    note_launch();
     k_gram_partial<CT, TS><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rps, part);
 }
 
@@ -139,6 +141,7 @@ int gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int 
         else if (ts == 32) launch_gram<double, 32>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
         else launch_gram<double, 16>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
     }
+    note_launch();
     k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -207,9 +210,11 @@ int update(const double *A, int64_t lda, int p, const double *M, int64_t ldm, in
     (void)attr_set_once;
     if (compute_f32) {
         const size_t sm = (size_t)(p * q + 32 * p) * sizeof(float);
+        note_launch();
         k_update<float><<<(int)blocks, 256, sm, st>>>(A, lda, p, M, ldm, q, C, ldc, D, ldd, n, alpha, beta);
     } else {
         const size_t sm = (size_t)(p * q + 32 * p) * sizeof(double);
+        note_launch();
         k_update<double><<<(int)blocks, 256, sm, st>>>(A, lda, p, M, ldm, q, C, ldc, D, ldd, n, alpha, beta);
     }
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
@@ -257,7 +262,9 @@ int colnorms(const double *A, int64_t lda, int k, int64_t n, double *out, int ta
     if ((int64_t)nb * 256 > n) nb = (int)((n + 255) / 256);
     if (nb < 1) nb = 1;
     const int64_t rpb = (n + nb - 1) / nb;
+    note_launch();
     k_colsq_partial<<<nb, 256, 0, st>>>(A, lda, k, n, rpb, part);
+    note_launch();
     k_colsq_reduce<<<1, 64, 0, st>>>(part, nb, k, out, take_sqrt);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -279,6 +286,7 @@ __global__ void k_widen(const T *__restrict__ src, int64_t lds, double *__restri
 int widen(int src_f32, const void *src, int64_t lds, double *dst, int64_t ldd, int k, int64_t n, cudaStream_t st)
 {
     const int grid = num_sms() * 8;
+    note_launch();
     if (src_f32)
         k_widen<float><<<grid, 256, 0, st>>>((const float *)src, lds, dst, ldd, k, n);
     else
@@ -300,6 +308,7 @@ __global__ void k_scale_cols_inv(double *__restrict__ A, int64_t lda, int k, int
 
 int scale_cols_inv(double *A, int64_t lda, int k, int64_t n, const double *norms, cudaStream_t st)
 {
+    note_launch();
     k_scale_cols_inv<<<num_sms() * 8, 256, 0, st>>>(A, lda, k, n, norms);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -317,6 +326,7 @@ __global__ void k_copy_block(const double *__restrict__ S, int64_t lds, double *
 
 int copy_block(const double *S, int64_t lds, double *D, int64_t ldd, int k, int64_t n, cudaStream_t st)
 {
+    note_launch();
     k_copy_block<<<num_sms() * 8, 256, 0, st>>>(S, lds, D, ldd, k, n);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }

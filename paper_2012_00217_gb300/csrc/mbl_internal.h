@@ -21,6 +21,12 @@ struct PcgDev {
     unsigned *counter;
 };
 
+// Count of the kernels this library has launched in the process.  Every launch site
+// calls note_launch(); a launch made while this thread captures a CUDA graph is not
+// counted there but once per replay of the graph (note_launch(kernel nodes)).
+void note_launch(int64_t count = 1);
+void set_capturing(bool on);
+
 int num_sms();
 int make_chain_params(const mbl_chain *chain, double sigma, ChainParams *cp);
 int apply_device(const ChainParams &cp, int dtype, const void *X, int64_t ldx, void *Y, int64_t ldy, uint32_t n,
@@ -34,6 +40,7 @@ size_t pcg_partial_doubles();
 int tile_bits_for(int L, int K, size_t es);
 void set_tile_bits(int K, size_t es, int bits);
 void set_lane_bytes(int K, size_t es, int bytes);
+void set_schedule(int K, size_t es, int mode);
 template <typename T>
 int pcg_fold_dinv(const ChainParams &cp, uint32_t n, T *dinv, cudaStream_t st);
 template <typename T>

@@ -33,6 +33,16 @@
 
 namespace mbl {
 
+static std::atomic<int64_t> g_kernel_launches{0};
+static thread_local bool t_capturing = false;
+
+void note_launch(int64_t count)
+{
+    if (!t_capturing) g_kernel_launches.fetch_add(count, std::memory_order_relaxed);
+}
+
+void set_capturing(bool on) { t_capturing = on; }
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -344,6 +354,7 @@ int read_status(Solver &s, HostStatus *h)
 // Capture body(have_p) once into an executable graph.
 struct GraphCache {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int64_t kernels[2] = {0, 0};  // kernel nodes per graph
     cudaStream_t cap = nullptr;
     ~GraphCache()
     {
@@ -366,9 +377,11 @@ int run_body(Solver &s, bool have_p, bool use_graph, GraphCache &gc)
             s.st = user;
             return MBL_ERR_CUDA;
         }
+        set_capturing(true);
         int rc = s.enqueue_body(have_p);
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(gc.cap, &g);
+        set_capturing(false);
         s.st = user;
         s.matvecs = mv;  // counted again at each replay below
         if (rc != MBL_OK) {
@@ -376,6 +389,16 @@ int run_body(Solver &s, bool have_p, bool use_graph, GraphCache &gc)
             return rc;
         }
         if (ce != cudaSuccess || !g) return MBL_ERR_CUDA;
+        size_t nn = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (size_t i = 0; i < nn; ++i) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                        ++gc.kernels[slot];
+                }
+        }
         ce = cudaGraphInstantiate(&gc.exec[slot], g, 0);
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) return MBL_ERR_CUDA;
@@ -383,7 +406,9 @@ int run_body(Solver &s, bool have_p, bool use_graph, GraphCache &gc)
     // matvec accounting of one body
     s.matvecs += (int64_t)(s.folded ? 2 * s.m * s.k + 2 * s.k + (have_p ? 2 * s.k : 0) + 2 * s.k
                                     : s.k + (have_p ? s.k : 0) + s.k);
-    return cudaGraphLaunch(gc.exec[slot], s.st) == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+    if (cudaGraphLaunch(gc.exec[slot], s.st) != cudaSuccess) return MBL_ERR_CUDA;
+    note_launch(gc.kernels[slot]);
+    return MBL_OK;
 }
 
 }  // namespace
@@ -813,3 +838,5 @@ extern "C" int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, cons
     if (first_error.load() != MBL_OK) return first_error.load();
     return not_converged.load() ? MBL_ERR_NOT_CONVERGED : MBL_OK;
 }
+
+extern "C" int64_t mbl_kernel_launch_count(void) { return g_kernel_launches.load(std::memory_order_relaxed); }

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "mbl_dense.h"
+#include "mbl_internal.h"
 
 namespace mbl {
 
@@ -241,6 +242,7 @@ int small_eig(int n, const double *G, int64_t ldg, double *w, double *Z, double 
     }();
     (void)attr_once;
     const int in_smem = n <= 64;
+    note_launch();
     k_small_eig<<<1, kSmallThreads, in_smem ? eig_smem_bytes(n) : 0, st>>>(n, G, ldg, w, Z, work, in_smem);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_chol_inv(int n, const d
 
 int small_chol_inv(int n, const double *G, int64_t ldg, double *Rinv, double *work, int *flag, cudaStream_t st)
 {
+    note_launch();
     k_small_chol_inv<<<1, kSmallThreads, 0, st>>>(n, G, ldg, Rinv, work, flag);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -447,6 +450,7 @@ int small_svqb_rr(int w, int k, int largest, int mixed, const double *GS, const 
     const size_t es = mixed ? sizeof(float) : sizeof(double);
     const size_t sm = 2 * (size_t)w * pad_ld(w) * es;
     const int use_smem = sm <= (size_t)cap;
+    note_launch();
     if (mixed)
         k_small_rr<float><<<1, kSmallThreads, use_smem ? sm : 0, st>>>(w, k, largest, GS, GA, tau, coef, theta,
                                                                        work, info, use_smem);
@@ -517,6 +521,7 @@ __global__ void k_hrr_select(int k, int nev, const double *mu, const double *V, 
 int hrr_select(int k, int nev, const double *mu, const double *V, const double *EtE, double tol_abs, double norm_h,
                double *res_all, int *sel, double *res_sel, int *st, double *dst, cudaStream_t s)
 {
+    note_launch();
     k_hrr_select<<<1, 64, 0, s>>>(k, nev, mu, V, EtE, tol_abs, norm_h, res_all, sel, res_sel, st, dst);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
@@ -532,6 +537,7 @@ __global__ void k_gather_cols(int k, int nev, const double *V, const int *sel, d
 
 int gather_cols(int k, int nev, const double *V, const int *sel, double *Csel, cudaStream_t st)
 {
+    note_launch();
     k_gather_cols<<<1, 256, 0, st>>>(k, nev, V, sel, Csel);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }

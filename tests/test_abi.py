@@ -1,0 +1,195 @@
+"""The C ABI without a GPU: the library loads, exports every function include/mbl.h
+declares, its structs have the header's layout, and the entry points that do no GPU
+work (sizes, argument checks, tuning switches, status text) behave as documented."""
+import ctypes
+import math
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mbl.h")
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_2012_00217_gb300 import build as pbuild
+    if pbuild.needs_build():
+        if shutil.which(pbuild.NVCC) is None and not os.path.exists(pbuild.NVCC):
+            pytest.skip("nvcc not available to build the library")
+        pbuild.build()
+    from paper_2012_00217_gb300 import binding
+    binding.lib.cache_clear()
+    return binding.lib()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mbl_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for need in ("mbl_basis_build", "mbl_basis_rank", "mbl_hamiltonian_apply", "mbl_lobpcg_solve",
+                 "mbl_lobpcg_solve_batched", "mbl_spectrum_bounds"):
+        assert need in names
+
+
+def test_every_declared_function_is_exported(so):
+    missing = [nm for nm in _declared() if not hasattr(so, nm)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(so):
+    from paper_2012_00217_gb300 import binding
+    assert sorted(binding.EXPORTED) == _declared()
+
+
+def _c_layout(tmp_path):
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "layout.c"
+    fields = {
+        "mbl_chain": ["L", "n_up", "periodic", "delta", "h_host"],
+        "mbl_lobpcg_opts": ["nev", "k", "max_iter", "pcg_iters", "tol", "pcg_tol", "norm_h", "mode",
+                            "use_graph", "timing"],
+        "mbl_lobpcg_stats": ["iters", "converged", "matvecs", "seconds", "max_rel_resid", "norm_h",
+                             "t_setup", "t_resid", "t_pcg", "t_wp", "t_gram", "t_small", "t_update",
+                             "t_refresh", "t_hrr"],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mbl.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (st, st))
+        for f in fs:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (st, f, st, f))
+    lines += ["return 0; }"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        st, f, v = line.split()
+        got[(st, f)] = int(v)
+    return got
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    from paper_2012_00217_gb300 import binding
+    c = _c_layout(tmp_path)
+    for st, cls in (("mbl_chain", binding.Chain), ("mbl_lobpcg_opts", binding.LobpcgOpts),
+                    ("mbl_lobpcg_stats", binding.LobpcgStats)):
+        assert c[(st, "sizeof")] == ctypes.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert c[(st, f)] == getattr(cls, f).offset, (st, f)
+
+
+def test_basis_size_is_the_binomial(so):
+    for L in range(1, 33):
+        for m in range(0, L + 1):
+            assert so.mbl_basis_size(L, m) == math.comb(L, m)
+    for L, m in ((0, 0), (33, 16), (10, 11), (10, -1), (-4, 2)):
+        assert so.mbl_basis_size(L, m) < 0
+
+
+def test_status_strings(so):
+    from paper_2012_00217_gb300 import binding
+    seen = set()
+    for code in (binding.MBL_OK, binding.MBL_ERR_ARG, binding.MBL_ERR_WORKSPACE, binding.MBL_ERR_CUDA,
+                 binding.MBL_ERR_NOT_CONVERGED, binding.MBL_ERR_BREAKDOWN, binding.MBL_ERR_NUMERIC):
+        s = binding.status_string(code)
+        assert s and s not in seen
+        seen.add(s)
+    assert binding.status_string(12345)
+
+
+def test_launch_counter_is_host_state(so):
+    a = so.mbl_kernel_launch_count()
+    assert a >= 0
+    assert so.mbl_kernel_launch_count() == a  # nothing launched in between
+
+
+def _ws(so, chain, opts):
+    from paper_2012_00217_gb300 import binding
+    sz = ctypes.c_size_t(0)
+    rc = so.mbl_lobpcg_workspace_size(ctypes.byref(chain), ctypes.byref(opts), ctypes.byref(sz))
+    return rc, sz.value
+
+
+def test_workspace_size_grows_with_block_and_checks_options(so):
+    import paper_2012_00217_gb300 as mbl
+    from paper_2012_00217_gb300 import binding
+    ch = mbl.make_chain(16, np.linspace(-1, 1, 16))
+    prev = 0
+    for k in (8, 16, 32, 64):
+        rc, b = _ws(so, ch, mbl.make_opts(4, k))
+        assert rc == binding.MBL_OK and b > prev
+        prev = b
+    # mixed mode keeps the PCG vectors in FP32: a smaller workspace than FP64
+    _, b64 = _ws(so, ch, mbl.make_opts(8, 16, mode=mbl.MODE_FP64))
+    _, bmx = _ws(so, ch, mbl.make_opts(8, 16, mode=mbl.MODE_MIXED))
+    assert 0 < bmx < b64
+    for bad in (mbl.make_opts(0, 8), mbl.make_opts(9, 8), mbl.make_opts(4, 65), mbl.make_opts(4, 8, mode=7),
+                mbl.make_opts(4, 8, tol=0.0), mbl.make_opts(4, 8, pcg_iters=-1)):
+        assert _ws(so, ch, bad)[0] == binding.MBL_ERR_ARG
+    # 3k > n: the block does not fit the sector
+    small = mbl.make_chain(6, np.zeros(6))  # n = 20
+    assert _ws(so, small, mbl.make_opts(4, 8))[0] == binding.MBL_ERR_ARG
+    # bad chains
+    keep = []
+    for L, n_up in ((40, 20), (12, 13), (1, 0)):
+        h = np.zeros(max(L, 1))
+        keep.append(h)
+        c = binding.Chain(L, n_up, 0, 1.0, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert _ws(so, c, mbl.make_opts(1, 1))[0] == binding.MBL_ERR_ARG
+    # odd L and other sectors are allowed
+    assert _ws(so, mbl.make_chain(13, np.zeros(13), n_up=4), mbl.make_opts(2, 4))[0] == binding.MBL_OK
+
+
+def test_batched_workspace_is_slots_times_largest(so):
+    import paper_2012_00217_gb300 as mbl
+    from paper_2012_00217_gb300 import binding
+    chains = [mbl.make_chain(L, np.zeros(L)) for L in (12, 14, 16)]
+    opts = mbl.make_opts(8, 16)
+    one = _ws(so, chains[-1], opts)[1]
+    b1 = binding.batched_workspace_size(chains, opts, 1)
+    b3 = binding.batched_workspace_size(chains, opts, 3)
+    assert b1 >= one and b3 >= 3 * one
+    assert b3 < 3 * one + 3 * 4096  # slot alignment only
+
+
+def test_tuning_switches_validate(so):
+    from paper_2012_00217_gb300 import binding
+    ok, bad = binding.MBL_OK, binding.MBL_ERR_ARG
+    for k, dt, bits, want in ((32, 0, 5, ok), (32, 1, -1, ok), (32, 0, 0, ok), (1, 0, 16, ok),
+                              (32, 0, 1, bad), (32, 0, 17, bad), (0, 0, 4, bad), (257, 0, 4, bad),
+                              (32, 2, 4, bad)):
+        assert so.mbl_set_product_tile_bits(k, dt, bits) == want
+    for k, dt, nb, want in ((32, 0, 16, ok), (32, 1, 32, ok), (8, 0, 0, ok), (32, 0, 8, bad),
+                            (32, 0, 64, bad), (0, 0, 16, bad)):
+        assert so.mbl_set_product_lane_bytes(k, dt, nb) == want
+    # restore the defaults
+    for k in (1, 32):
+        for dt in (0, 1):
+            so.mbl_set_product_tile_bits(k, dt, 0)
+    for k in (8, 32):
+        for dt in (0, 1):
+            so.mbl_set_product_lane_bytes(k, dt, 0)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2012_00217_gb300 import binding
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "absent.so"))
+    binding.lib.cache_clear()
+    try:
+        with pytest.raises(RuntimeError, match="not built"):
+            binding.lib()
+    finally:
+        monkeypatch.undo()
+        binding.lib.cache_clear()
