@@ -246,7 +246,8 @@ def _graph_time(torch, fn, reps, flush=None):
 
 def matvec_roofline(torch, mbl, dev, peak_gbs, quick=False):
     """Block product bandwidth on the open-chain sweep (FP32 and FP64), L2 flushed
-    before every launch; algorithmic bytes = read X once + write Y once = 2 n k b."""
+    before every launch; algorithmic bytes = read X once + write Y once = 2 n k b.  Each
+    configuration is autotuned first (untimed)."""
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     rows = []
     sweep = wl.MATVEC_SWEEP if not quick else wl.MATVEC_SWEEP[:1]
@@ -265,12 +266,30 @@ def matvec_roofline(torch, mbl, dev, peak_gbs, quick=False):
                 X = torch.randn((n, k), generator=g, device=dev, dtype=tdt)
                 Y = torch.empty_like(X)
                 reps = 5 if n * k * es > 1e9 else 20
+                choice = mbl.binding.autotune_product(chain, X, Y, reps=3 if n * k * es > 1e9 else 10)
                 t = _graph_time(torch, lambda: mbl.hamiltonian_apply(chain, 0.0, X, Y), reps, flush)
                 gbs = 2.0 * n * k * es / t / 1e9
                 rows.append(dict(L=L, k=k, dtype=dtype, n=n, us=t * 1e6, gbs=gbs, frac=gbs / peak_gbs,
-                                 l2_resident=bool(2 * n * k * es < 126e6)))
+                                 l2_resident=bool(2 * n * k * es < 126e6),
+                                 tuned={kk: choice[kk] for kk in ("schedule", "lane_bytes", "tile_bits")}))
                 del X, Y
     return rows
+
+
+def autotune_step(torch, mbl, dev, s):
+    """Run the library's product autotuner (untimed) for the block products of the step:
+    FP32 at the block width (the PCG products) and FP64 at the block width (the outer
+    products of mixed mode)."""
+    out = {}
+    for name, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        g = torch.Generator(device=dev)
+        g.manual_seed(11)
+        X = torch.randn((s["n"], s["k"]), generator=g, device=dev, dtype=tdt)
+        Y = torch.empty_like(X)
+        out[name] = mbl.binding.autotune_product(s["chain"], X, Y, reps=10)
+        del X, Y
+    torch.cuda.synchronize()
+    return out
 
 
 def solve_kernel_roofline(torch, mbl, dev, s, peak_gbs):
@@ -449,6 +468,7 @@ def main():
         torch.cuda.synchronize()
 
     s = _setup(torch, mbl, dev, rank_seed(CFG["seed"], rank))
+    tuned = autotune_step(torch, mbl, dev, s)
     step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
@@ -526,6 +546,7 @@ def main():
                      "peak_kind": peak_kind + " (hbm_gbs)"},
         "matvec_roofline": None,
         "solve_kernel": kern,
+        "autotuned": tuned,
         "solve_phases_s": phases,
         "bounds_s": t_b,
         "batched": batch,

@@ -51,8 +51,11 @@ typedef struct CUstream_st *mbl_stream_t; /* identical to cudaStream_t */
 
 #define MBL_MODE_FP64 0  /* every step in FP64 */
 #define MBL_MODE_MIXED 1 /* FP32 preconditioner and FP32 Gram matrices; FP64 products
-                            of H for X, W, P, FP64 Rayleigh-Ritz, orthonormalisation of
-                            X and residuals (Sec. 6.2: PCG in single, LOBPCG in double) */
+                            of H for X, W, P, FP64 Rayleigh-Ritz with H, orthonormalisation
+                            of X and residual norms (Sec. 6.2: PCG in single, LOBPCG in
+                            double).  If the largest wanted residual has not fallen by 10 %
+                            in 20 iterations, the Rayleigh-Ritz Grams of the fold switch to
+                            FP64 for the rest of the solve. */
 
 /* Human-readable text for a status code (static storage). */
 const char *mbl_status_string(int status);
@@ -112,19 +115,42 @@ int mbl_hamiltonian_apply(const mbl_chain *chain, double sigma, int dtype, const
 int mbl_set_product_tile_bits(int k, int dtype, int bits);
 
 /* Tuning: bytes of each row that one lane moves per neighbour in the tiled product
- * (16 or 32; 0 = default 32) for block width k and type dtype.  Returns MBL_ERR_ARG
+ * (16, 32 or 64; 0 = default 32) for block width k and type dtype.  Returns MBL_ERR_ARG
  * for any other value, k outside 1..256 or an unknown dtype. */
 int mbl_set_product_lane_bytes(int k, int dtype, int bytes);
 
-/* Tuning: work order of the plain tiled product (mbl_hamiltonian_apply and the FP64
- * products inside the solver) for block width k and type dtype.  0 = by size (default:
- * ordered for rows of k * element size >= 256 bytes once C(L, n_up) * k * element size
- * reaches 1 GiB in FP32 or 128 MiB in FP64), 1 = persistent (a few blocks
- * per SM striding over the tiles), 2 = ordered (one 32-row chunk per warp; the
- * hardware dispatches blocks in index order, so the tiles being read advance as a
- * narrow window that stays in L2).  Results are bitwise identical under every order.
- * Returns MBL_ERR_ARG for schedule outside 0..2, k outside 1..256 or an unknown dtype. */
+/* Tuning: work order of the tiled product for block width k and type dtype.
+ * 0 = by size (default: ordered for plain products with rows of k * element size >= 256
+ * bytes once C(L, n_up) * k * element size reaches 1 GiB in FP32 or 128 MiB in FP64,
+ * else persistent), 1 = persistent (a few blocks per SM striding over the tiles),
+ * 2 = ordered (plain products only: one chunk of rows per warp; the hardware dispatches
+ * blocks in index order, so the tiles being read advance as a narrow window that stays
+ * in L2), 3 = staged (each block copies whole tiles of at most 48 KB into shared memory
+ * with bulk asynchronous copies and reads the in-tile neighbours there; needs rows of a
+ * multiple of 16 bytes, ld = k and 16-byte aligned buffers, else persistent).  Results
+ * are bitwise identical under orders 0-2 for the same tile width.  Returns MBL_ERR_ARG for
+ * schedule outside 0..3, k outside 1..256 or an unknown dtype. */
 int mbl_set_product_schedule(int k, int dtype, int schedule);
+
+/* Autotuner of the product (the tile widths and work orders above): times the plain
+ * product of this chain, block width k, type dtype, under every candidate -- schedule
+ * persistent / ordered / staged (where its conditions hold) times 32- or 64-byte lanes
+ * (64 only for rows of >= 64 bytes) -- on the caller's buffers X_dev, Y_dev (n x k,
+ * ld = k, n = C(L, n_up); X is read, Y overwritten; they must not overlap): one warm-up
+ * and `reps` timed launches each (1 <= reps <= 1000), CUDA events on `stream`.  The
+ * fastest is kept for all later products with this L, k and dtype in this process (the
+ * explicit switches above still take precedence) and reported in *choice (optional):
+ * schedule 1..3, lane bytes, tile bits and the mean microseconds per product.  Widths k
+ * without a tiled kernel leave nothing to choose: MBL_OK with *choice zeroed.
+ * Host-synchronous (waits for its timing launches). */
+typedef struct {
+    int schedule;
+    int lane_bytes;
+    int tile_bits;
+    double microseconds;
+} mbl_product_choice;
+int mbl_autotune_product(const mbl_chain *chain, int dtype, const void *X_dev, void *Y_dev, int64_t n, int k,
+                         int reps, mbl_product_choice *choice, mbl_stream_t stream);
 
 /* ---- folded-spectrum LOBPCG (Sec. 3.2, Sec. 6.2) ---------------------------------- */
 

@@ -33,7 +33,7 @@ EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis
             "mbl_bounds_workspace_size", "mbl_spectrum_bounds", "mbl_lobpcg_solve_noalloc",
             "mbl_set_product_tile_bits", "mbl_set_product_lane_bytes", "mbl_batched_workspace_size",
             "mbl_lobpcg_solve_batched", "mbl_kernel_launch_count",
-            "mbl_set_product_schedule")
+            "mbl_set_product_schedule", "mbl_autotune_product")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -53,6 +53,11 @@ class LobpcgOpts(ctypes.Structure):
                 ("pcg_iters", ctypes.c_int), ("tol", ctypes.c_double), ("pcg_tol", ctypes.c_double),
                 ("norm_h", ctypes.c_double), ("mode", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("timing", ctypes.c_int)]
+
+
+class ProductChoice(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int), ("lane_bytes", ctypes.c_int), ("tile_bits", ctypes.c_int),
+                ("microseconds", ctypes.c_double)]
 
 
 class LobpcgStats(ctypes.Structure):
@@ -96,6 +101,8 @@ def lib():
     so.mbl_set_product_lane_bytes.argtypes = [i32, i32, i32]
     so.mbl_set_product_schedule.restype = i32
     so.mbl_set_product_schedule.argtypes = [i32, i32, i32]
+    so.mbl_autotune_product.restype = i32
+    so.mbl_autotune_product.argtypes = [pch, i32, p, p, i64, i32, i32, ctypes.POINTER(ProductChoice), p]
     so.mbl_set_product_tile_bits.restype = i32
     so.mbl_set_product_tile_bits.argtypes = [i32, i32, i32]
     so.mbl_lobpcg_workspace_size.restype = i32
@@ -218,6 +225,22 @@ def set_product_schedule(k, dtype, schedule):
     torch = _torch()
     dt = MBL_F32 if dtype == torch.float32 else MBL_F64
     _check(lib().mbl_set_product_schedule(int(k), dt, int(schedule)), "mbl_set_product_schedule")
+
+
+def autotune_product(chain, X, Y, reps=5):
+    """mbl_autotune_product on the contiguous n x k CUDA tensors X (read) and Y
+    (overwritten); returns the kept choice as a dict."""
+    torch = _torch()
+    if X.dtype not in (torch.float32, torch.float64) or Y.dtype != X.dtype or X.dim() != 2 or Y.shape != X.shape:
+        raise ValueError("X, Y: equal n x k float32/float64 CUDA tensors")
+    if not (X.is_contiguous() and Y.is_contiguous()):
+        raise ValueError("X, Y must be contiguous (ld = k)")
+    dt = MBL_F32 if X.dtype == torch.float32 else MBL_F64
+    n, k = X.shape
+    ch = ProductChoice()
+    _check(lib().mbl_autotune_product(ctypes.byref(chain), dt, _dev(X, X.dtype, "X"), _dev(Y, Y.dtype, "Y"), int(n),
+                                      int(k), int(reps), ctypes.byref(ch), _stream_ptr(X)), "mbl_autotune_product")
+    return {f: getattr(ch, f) for f, _ in ch._fields_}
 
 
 def make_opts(nev, k, tol=1e-8, max_iter=200, pcg_iters=50, pcg_tol=0.0, norm_h=0.0,

@@ -43,7 +43,7 @@ struct RowLayout {
 template <typename T, int K, int LB = 32>
 struct WideRowLayout {
     static constexpr int kBytes = K * (int)sizeof(T);
-    static constexpr int V = kBytes >= LB ? LB / (int)sizeof(T) : (kBytes >= 16 ? 16 / (int)sizeof(T) : K);
+    static constexpr int V = kBytes >= LB ? LB / (int)sizeof(T) : K;
     static constexpr int G = K / V;
     static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
     // rows per work item of the tiled product: at least four row-passes of the warp
@@ -122,6 +122,14 @@ __device__ __forceinline__ void stv_stream(T *p, const Vec<T, V> &x)
         stv<T, V>(p, x);
     }
 }
+
+// Products that must not be fused with a neighbouring add: the tiled kernels round
+// d * x and delta/2 * count on their own, so every variant adds the same rounded terms
+// in the same order and their results agree bit for bit.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Gather the neighbour rows listed in nbl[0..f) into acc: chunks of 8 independent
 // 16-byte loads are issued before any of them is consumed.
@@ -275,13 +283,91 @@ __device__ __forceinline__ void finish_column_sums(const Reduce &rd, int k, doub
 // PCG epilogue of a product launch: block partials of t.t (kPcgT) or r.(M^-1 r)
 // (kPcgQ), then in the last block alpha = rz / t.t, or beta = rz_new / rz with the
 // freeze rule (a column stops once rz_new <= tol^2 rz0, or on NaN/Inf).
+// FP32 variant of the two reductions, for the FP32 kernels: block partials and the
+// last block's sum over blocks are compensated FP32 pairs (s + c, TwoSum), stored as
+// float2 in the partial slots, and only the k final totals are widened to FP64.  The
+// FP64 pipe (about 1/64 of the FP32 rate) would otherwise set a serial tail of
+// several microseconds per launch in the last block.
+template <int V, int G>
+__device__ __forceinline__ bool block_column_reduce_f32(float (*red)[64], float (&part)[V], int k, const Reduce &rd)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        for (int off = G; off < 32; off <<= 1) part[v] += __shfl_xor_sync(0xffffffffu, part[v], off);
+    if (lane < G) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) red[warp][lane * V + v] = part[v];
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        float sum = 0.0f, cmp = 0.0f;
+        for (int w = 0; w < kWarps; ++w) {
+            float hi, e;
+            two_sum(sum, red[w][threadIdx.x], hi, e);
+            sum = hi;
+            cmp += e;
+        }
+        reinterpret_cast<float2 *>(rd.partials)[(int64_t)blockIdx.x * k + threadIdx.x] = make_float2(sum, cmp);
+    }
+    __threadfence();
+    __shared__ unsigned s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ticket = atomicAdd(rd.counter, 1u);
+        s_last = (ticket == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    return true;
+}
+
+__device__ __forceinline__ void finish_column_sums_f32(const Reduce &rd, int k, double *total)
+{
+    __shared__ float2 s_tree2[kThreads];
+    const int per = kThreads / k;
+    const int c = threadIdx.x / per, j = threadIdx.x % per;
+    float sum = 0.0f, cmp = 0.0f;
+    if (c < k) {
+        const float2 *pp = reinterpret_cast<const float2 *>(rd.partials);
+        for (int b = j; b < (int)gridDim.x; b += per) {
+            const float2 q = pp[(int64_t)b * k + c];
+            float hi, e;
+            two_sum(sum, q.x, hi, e);
+            sum = hi;
+            cmp += e + q.y;
+        }
+    }
+    s_tree2[threadIdx.x] = make_float2(sum, cmp);
+    __syncthreads();
+    if (c < k && j == 0) {
+        float S = 0.0f, C = 0.0f;
+        for (int q = 0; q < per; ++q) {
+            const float2 v = s_tree2[threadIdx.x + q];
+            float hi, e;
+            two_sum(S, v.x, hi, e);
+            S = hi;
+            C += e + v.y;
+        }
+        total[c] = (double)S + (double)C;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *rd.counter = 0u;
+}
+
 template <typename T, int V, int G, int MODE>
 __device__ __forceinline__ void pcg_block_finish(T (*red)[64], T (&part)[V], int K, const PcgScalars &ps,
                                                  const Reduce &rd)
 {
-    if (!block_column_reduce<T, V, G>(red, part, K, rd)) return;
     __shared__ double s_tot[64];
-    finish_column_sums(rd, K, s_tot);
+    if constexpr (sizeof(T) == 4) {
+        if (!block_column_reduce_f32<V, G>(red, part, K, rd)) return;
+        finish_column_sums_f32(rd, K, s_tot);
+    } else {
+        if (!block_column_reduce<T, V, G>(red, part, K, rd)) return;
+        finish_column_sums(rd, K, s_tot);
+    }
     if (threadIdx.x < K) {
         const int c = threadIdx.x;
         if (MODE == kPcgT) {
@@ -457,14 +543,171 @@ __host__ __device__ inline int lowtab_base(int B) { return (1 << B) - 4; }
 #define MBL_TILED_MIN_BLOCKS 3
 #endif
 
+// Per-tile values of a tile t (p = n_up - popc(t) up spins in its low part), computed
+// by one warp, one lane each: the tile's first row (lane 0), the diagonal constant of
+// its high bits, the rank shift of every high bond whose two spins differ (lane b + 1
+// for bond (B + b, B + b + 1): C(B + b, p + popc(t mod 2^b)), + when the up spin moves
+// up, - when it moves down; compacted in bond order), and the first row of the tile
+// across the wrap bond (lane 31).
+template <typename T>
+struct TileMeta {
+    uint32_t off, offper;
+    int nh;
+    T ct;
+    uint32_t shift[32];
+};
+
+template <typename T>
+__device__ __forceinline__ void tile_meta_warp(const uint32_t *sbin, const T *tab, const ChainParams &cp, int B,
+                                               uint32_t t, int p, TileMeta<T> &tm)
+{
+    const int lane = threadIdx.x & 31, m = cp.n_up, H = cp.L - B;
+    uint32_t v32 = 0;
+    bool flip = false;
+    if (lane == 0) {
+        v32 = cns_rank(sbin, (t << B) | ((1u << p) - 1u));
+        const uint32_t ahigh = __popc((t ^ (t >> 1)) & ((1u << (H - 1)) - 1u));
+        tm.ct = (cp_diag_const<T>(cp) + field_sum(tab, t << B)) - mul_rn(cp_half_delta<T>(cp), (T)ahigh);
+    } else if (lane <= H - 1) {
+        const int b = lane - 1;
+        if (((t >> b) ^ (t >> (b + 1))) & 1u) {
+            flip = true;
+            const uint32_t dlt = binom(sbin, B + b, p + __popc(t & ((1u << b) - 1u)));
+            v32 = ((t >> b) & 1u) ? dlt : (0u - dlt);  // modulo 2^32, applied as int32
+        }
+    } else if (lane == 31 && cp.periodic) {
+        const uint32_t t2 = t ^ (1u << (H - 1));
+        const int p2 = m - __popc(t2);
+        v32 = (p2 >= 0 && p2 <= B) ? cns_rank(sbin, (t2 << B) | ((1u << p2) - 1u)) : kNoRow;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, flip);
+    if (flip) tm.shift[__popc(bal & ((1u << lane) - 1u))] = v32;
+    if (lane == 0) {
+        tm.off = v32;
+        tm.nh = __popc(bal);
+    }
+    if (lane == 31) tm.offper = v32;
+}
+
+// One pass of a warp over RPW rows of a tile (row j of this lane group, `valid` when
+// j < tile size).  Own row and in-tile neighbours come from Xt (row stride ldt: the
+// tile in shared memory, or X itself from the tile's first row); the joining, wrap and
+// high-bond rows from X.  y = (d - sigma) x + 1/2 (sum of neighbour rows), the
+// neighbours summed first in a fixed order (joining, wrap, low bonds, high bonds):
+// scaling by 1/2 is exact, so only the order of the additions is a choice, and every
+// variant (persistent, ordered, staged) makes the same one.
+template <typename T, int V, int NB, int MODE>
+__device__ __forceinline__ void tile_row_pass(const ChainParams &cp, int B, const T *__restrict__ X, int64_t ldx,
+                                              const T *__restrict__ Xt, int64_t ldt, const LowRec *__restrict__ rp,
+                                              uint32_t j, bool valid, const TileMeta<T> &tm, const T *tab, T hdelta,
+                                              uint32_t t0, uint32_t thi, uint32_t sup, uint32_t sdn, int col,
+                                              T *__restrict__ Y, int64_t ldy, T *__restrict__ R,
+                                              const T *__restrict__ dinv, const T *s_alpha, T (&part)[V])
+{
+    const uint32_t r = tm.off + j;
+    const T *__restrict__ xr = X + (int64_t)r * ldx + col;
+    uint4 w0 = make_uint4(0, 0, 0, 0), w1 = make_uint4(0, 0, 0, 0);
+    if (valid) {
+        w0 = __ldg(reinterpret_cast<const uint4 *>(rp + j));
+        w1 = __ldg(reinterpret_cast<const uint4 *>(rp + j) + 1);
+    }
+    const uint32_t u = w0.x & 0xffffu, cnt = (w0.x >> 16) & 0xffu, alow = w0.x >> 24;
+    const uint32_t ub = (u >> (B - 1)) & 1u;
+    const bool join = valid && ub != t0;
+    const bool wrap = valid && cp.periodic && (u & 1u) != thi;
+    T nb[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) nb[v] = (T)0;
+    {
+        // (every conditionally loaded vector starts at zero: adding +0 is exact, and
+        // values left undefined on some lanes make the register allocator spill)
+        Vec<T, V> ja, wb;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            ja.v[v] = (T)0;
+            wb.v[v] = (T)0;
+        }
+        if (join) ja = ldv<T, V>(xr + (ub ? (int64_t)sup : -(int64_t)sdn) * ldx);
+        if (wrap) wb = ldv<T, V>(X + (int64_t)(tm.offper + (w0.y & 0xffffu)) * ldx + col);
+#pragma unroll
+        for (int v = 0; v < V; ++v) nb[v] += ja.v[v];
+        if (cp.periodic) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) nb[v] += wb.v[v];
+        }
+    }
+    {
+        // in-tile neighbours; the loop runs to the warp's largest count (no arithmetic
+        // past it: FP64 is ALU-bound here)
+        const uint32_t nbw[6] = {w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const int cmax = (int)__reduce_max_sync(0xffffffffu, valid ? cnt : 0u);
+#pragma unroll
+        for (int q0 = 0; q0 < 12; q0 += NB) {
+            if (q0 >= cmax) break;
+            Vec<T, V> a[NB];
+#pragma unroll
+            for (int e = 0; e < NB; ++e) {
+                const int q = q0 + e;
+                const int qq = q < 12 ? q : 11;  // slots past 12 are never loaded
+                const uint32_t jn = (nbw[qq >> 1] >> (16 * (qq & 1))) & 0xffffu;
+#pragma unroll
+                for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
+                if (q < (int)cnt) a[e] = ldv<T, V>(Xt + (int64_t)jn * ldt + col);
+            }
+#pragma unroll
+            for (int e = 0; e < NB; ++e)
+                if (q0 + e < cmax) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) nb[v] += a[e].v[v];
+                }
+        }
+    }
+    for (int h0 = 0; h0 < tm.nh; h0 += NB) {
+        // high-bond neighbours: the tile's rows moved as a block, one shift per bond
+        Vec<T, V> a[NB];
+#pragma unroll
+        for (int e = 0; e < NB; ++e) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
+            if (valid && h0 + e < tm.nh) a[e] = ldv<T, V>(xr + (int64_t)(int32_t)tm.shift[h0 + e] * ldx);
+        }
+#pragma unroll
+        for (int e = 0; e < NB; ++e)
+            if (h0 + e < tm.nh) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) nb[v] += a[e].v[v];
+            }
+    }
+    Vec<T, V> x;
+#pragma unroll
+    for (int v = 0; v < V; ++v) x.v[v] = (T)0;
+    if (valid) x = ldv<T, V>(Xt + (int64_t)j * ldt + col);
+    const T d = (tm.ct + (tab[u & 255u] + tab[256 + (u >> 8)])) -
+                mul_rn(hdelta, (T)(alow + (join ? 1u : 0u) + (wrap ? 1u : 0u)));
+    T acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = fma_rn((T)0.5, nb[v], mul_rn(d, x.v[v]));
+    if (valid) {
+        T alpha[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) alpha[v] = (MODE == kPcgQ) ? s_alpha[col + v] : (T)0;
+        finish_row<T, V, MODE>(acc, 0, r, Y, ldy, R, dinv, col, alpha, part);
+    }
+}
+
 template <typename T, int K, int MODE, int LB>
-__global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(ChainParams cp, int B, const T *__restrict__ X,
-                                                          int64_t ldx, T *__restrict__ Y, int64_t ldy,
-                                                          T *__restrict__ R, const T *__restrict__ dinv,
-                                                          PcgScalars ps, Reduce rd)
+__global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(ChainParams cp, int B,
+                                                                               const T *__restrict__ X, int64_t ldx,
+                                                                               T *__restrict__ Y, int64_t ldy,
+                                                                               T *__restrict__ R,
+                                                                               const T *__restrict__ dinv,
+                                                                               PcgScalars ps, Reduce rd)
 {
     using Lay = WideRowLayout<T, K, LB>;
     constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G, CH = Lay::CH;
+    // neighbour loads issued together: 128 bytes per lane (two to eight vectors)
+    constexpr int NBr = 128 / (V * (int)sizeof(T));
+    constexpr int NB = NBr < 2 ? 2 : (NBr > 8 ? 8 : NBr);
     if (MODE == kPlain) {
         // ordered schedule (at most one item per warp): a block whose items hold no rows
         // leaves before any setup
@@ -487,8 +730,11 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(
     __shared__ T tab[1024];
     __shared__ T red[kWarps][64];
     __shared__ uint32_t spref[kLowMaxB + 2];  // spref[p] = sum_{q < p} C(B, q)
+    __shared__ T s_alpha[64];
+    __shared__ TileMeta<T> s_meta[kWarps];
     load_binom(sbin);
     build_field_tables<T>(tab, cp);
+    if (MODE == kPcgQ && threadIdx.x < K) s_alpha[threadIdx.x] = (T)ps.alpha[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t acc = 0;
@@ -503,17 +749,15 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(
     const uint32_t ntile = 1u << H;
     const uint32_t nchunk = (binom(sbin, B, B / 2) + CH - 1) / CH;
     const uint32_t total = ntile * nchunk;
-    const T hdelta = (T)cp.half_delta, half = (T)0.5;
-    const int lane = threadIdx.x & 31, grp = lane / G;
+    const T hdelta = cp_half_delta<T>(cp);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G;
     const int col = (lane % G) * V;
     const LowRec *__restrict__ tbl = g_lowtab + lowtab_base(B);
-    T part[V], alpha[V];
+    TileMeta<T> &tm = s_meta[warp];
+    T part[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        part[v] = (T)0;
-        alpha[v] = (MODE == kPcgQ) ? (T)ps.alpha[col + v] : (T)0;
-    }
-    const uint32_t gw = blockIdx.x * kWarps + (threadIdx.x >> 5), nw = gridDim.x * kWarps;
+    for (int v = 0; v < V; ++v) part[v] = (T)0;
+    const uint32_t gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
     for (uint32_t item = gw; item < total; item += nw) {
         // tile-major: the warps in flight cover a run of consecutive tiles, so in-tile
         // neighbours and the tiles reached by the low high-part bonds stay in L2
@@ -524,132 +768,169 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(
         const uint32_t j_begin = c * CH;
         if (j_begin >= Rt) continue;
         const uint32_t j_end = min(Rt, j_begin + CH);
-        // per-tile values, one lane each
-        uint32_t v32 = 0;
-        double ct = 0.0;
-        bool flip = false;
-        if (lane == 0) {
-            v32 = cns_rank(sbin, (t << B) | ((1u << p) - 1u));  // tile offset
-            const uint32_t ahigh = __popc((t ^ (t >> 1)) & ((1u << (H - 1)) - 1u));
-            ct = cp.diag_const + (double)field_sum(tab, t << B) - cp.half_delta * (double)ahigh;
-        } else if (lane <= H - 1) {  // high bond (B + b, B + b + 1), b = lane - 1
-            const int b = lane - 1;
-            if (((t >> b) ^ (t >> (b + 1))) & 1u) {
-                flip = true;
-                const uint32_t dlt = binom(sbin, B + b, p + __popc(t & ((1u << b) - 1u)));
-                v32 = ((t >> b) & 1u) ? dlt : (0u - dlt);  // rank shift, modulo 2^32
-            }
-        } else if (lane == 31 && cp.periodic) {  // tile across the wrap bond
-            const uint32_t t2 = t ^ (1u << (H - 1));
-            const int p2 = m - __popc(t2);
-            v32 = (p2 >= 0 && p2 <= B) ? cns_rank(sbin, (t2 << B) | ((1u << p2) - 1u)) : kNoRow;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, flip);
-        const int nh = __popc(bal);
-        // compact the high-bond shifts into lanes 0..nh-1
-        uint32_t hshift = 0;
-        {
-            unsigned bb = bal;
-            for (int q = 0; q < nh; ++q) {
-                const int owner = __ffs(bb) - 1;
-                bb &= bb - 1;
-                const uint32_t vq = __shfl_sync(0xffffffffu, v32, owner);
-                if (lane == q) hshift = vq;
-            }
-        }
-        const uint32_t off = __shfl_sync(0xffffffffu, v32, 0);
-        const uint32_t offper = __shfl_sync(0xffffffffu, v32, 31);
-        const T ctt = (T)__shfl_sync(0xffffffffu, ct, 0);
+        __syncwarp();
+        tile_meta_warp<T>(sbin, tab, cp, B, t, p, tm);
+        __syncwarp();
         const uint32_t t0 = t & 1u, thi = (t >> (H - 1)) & 1u;
-        const uint32_t sup = p >= 1 ? binom(sbin, B - 1, p - 1) : 0u;   // joining bond, up spin moves up
-        const uint32_t sdn = binom(sbin, B - 1, p);                      // joining bond, moves down
+        const uint32_t sup = p >= 1 ? binom(sbin, B - 1, p - 1) : 0u;  // joining bond, up spin moves up
+        const uint32_t sdn = binom(sbin, B - 1, p);                     // joining bond, moves down
         const LowRec *__restrict__ rp = tbl + spref[p];
+        const T *__restrict__ Xt = X + (int64_t)tm.off * ldx;
         for (uint32_t j0 = j_begin; j0 < j_end; j0 += RPW) {
             const uint32_t j = j0 + grp;
-            const bool valid = j < j_end;
-            const uint32_t r = off + j;
-            const T *__restrict__ xr = X + (int64_t)r * ldx + col;
-            // the row's low-pattern record: u, counts, wrap rank, local neighbours
-            uint4 w0 = make_uint4(0, 0, 0, 0), w1 = make_uint4(0, 0, 0, 0);
-            if (valid) {
-                w0 = __ldg(reinterpret_cast<const uint4 *>(rp + j));
-                w1 = __ldg(reinterpret_cast<const uint4 *>(rp + j) + 1);
-            }
-            const uint32_t u = w0.x & 0xffffu, cnt = (w0.x >> 16) & 0xffu, alow = w0.x >> 24;
-            const uint32_t ub = (u >> (B - 1)) & 1u;
-            const bool join = valid && ub != t0;
-            const bool wrap = valid && cp.periodic && (u & 1u) != thi;
-            T acc[V];
-            {
-                const T d = (ctt + (tab[u & 255u] + tab[256 + (u >> 8)])) -
-                            hdelta * (T)(alow + (join ? 1u : 0u) + (wrap ? 1u : 0u));
-                Vec<T, V> x;
-#pragma unroll
-                for (int v = 0; v < V; ++v) x.v[v] = (T)0;
-                if (valid) x = ldv<T, V>(xr);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = d * x.v[v];
-            }
-            // joining and wrap bonds
-            {
-                Vec<T, V> a, b;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    a.v[v] = (T)0;
-                    b.v[v] = (T)0;
-                }
-                if (join) a = ldv<T, V>(xr + (ub ? (int64_t)sup : -(int64_t)sdn) * ldx);
-                if (wrap) b = ldv<T, V>(X + (int64_t)(offper + (w0.y & 0xffffu)) * ldx + col);
-                if (cp.periodic) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] += half * (a.v[v] + b.v[v]);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] += half * a.v[v];
-                }
-            }
-            // low-part neighbours, in-tile ranks unpacked from the record; adds stop at the
-            // warp's largest count (no arithmetic on padding: FP64 is ALU-bound here)
-            {
-                const uint32_t nbw[6] = {w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-                const int cmax = (int)__reduce_max_sync(0xffffffffu, valid ? cnt : 0u);
-#pragma unroll
-                for (int q0 = 0; q0 < 12; q0 += 4) {
-                    if (q0 >= cmax) break;
-                    Vec<T, V> a[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int q = q0 + e;
-                        const uint32_t jn = (nbw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
-#pragma unroll
-                        for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
-                        if (q < (int)cnt) a[e] = ldv<T, V>(X + (int64_t)(off + jn) * ldx + col);
-                    }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (q0 + e < cmax)
-#pragma unroll
-                            for (int v = 0; v < V; ++v) acc[v] += half * a[e].v[v];
-                }
-            }
-            // high-part neighbours: the same shift for the whole tile, four loads in flight
-            for (int h0 = 0; h0 < nh; h0 += 4) {
-                Vec<T, V> a[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const uint32_t sh = __shfl_sync(0xffffffffu, hshift, (h0 + e) & 31);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
-                    if (valid && h0 + e < nh) a[e] = ldv<T, V>(xr + (int64_t)(int32_t)sh * ldx);
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (h0 + e < nh)
-#pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] += half * a[e].v[v];
-            }
-            if (valid) finish_row<T, V, MODE>(acc, 0, r, Y, ldy, R, dinv, col, alpha, part);
+            tile_row_pass<T, V, NB, MODE>(cp, B, X, ldx, Xt, ldx, rp, j, j < j_end, tm, tab, hdelta, t0, thi, sup,
+                                          sdn, col, Y, ldy, R, dinv, s_alpha, part);
         }
+    }
+    if (MODE == kPlain) return;
+    pcg_block_finish<T, V, G, MODE>(red, part, K, ps, rd);
+}
+
+// ---------------------------------------------------------------------------------
+// Staged tiled product: a block takes whole tiles (B chosen so a tile fits in 48 KB of
+// shared memory), copies the tile's rows into shared memory with one bulk asynchronous
+// copy (the tile is contiguous in X), and serves the in-tile (low-bond) neighbours from
+// there; the own row too.  Only the high-bond rows (own row + per-tile shift), the joining
+// row and the wrap row come from L2/HBM.  Requires ldx = ldy = K and rows of a multiple of
+// 16 bytes.  Same arithmetic, in the same order, as k_apply_tiled with the same tile width.
+
+constexpr int kStageBytes = 48 * 1024;
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz: bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete, for at most kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, unsigned parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// One bulk copy global -> shared (addresses 16-byte aligned, size a multiple of 16),
+// completing on mbar.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <typename T, int K, int MODE, int LB>
+__global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS)
+    k_apply_staged(ChainParams cp, int B, const T *__restrict__ X, T *__restrict__ Y, T *__restrict__ R,
+                   const T *__restrict__ dinv, PcgScalars ps, Reduce rd)
+{
+    using Lay = WideRowLayout<T, K, LB>;
+    constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G, RPB = kWarps * RPW;
+    constexpr int NBr = 128 / (V * (int)sizeof(T));
+    constexpr int NB = NBr < 2 ? 2 : (NBr > 8 ? 8 : NBr);
+    static_assert((K * sizeof(T)) % 16 == 0, "staged rows must be multiples of 16 bytes");
+    extern __shared__ __align__(128) unsigned char stage_raw[];
+    T *__restrict__ s_tile = reinterpret_cast<T *>(stage_raw);
+    __shared__ uint32_t sbin[kBinomDim * kBinomDim];
+    __shared__ T tab[1024];
+    __shared__ T red[kWarps][64];
+    __shared__ uint32_t spref[kLowMaxB + 2];
+    __shared__ T s_alpha[64];
+    __shared__ TileMeta<T> s_meta;
+    __shared__ __align__(8) uint64_t s_mbar;
+    load_binom(sbin);
+    build_field_tables<T>(tab, cp);
+    if (MODE == kPcgQ && threadIdx.x < K) s_alpha[threadIdx.x] = (T)ps.alpha[threadIdx.x];
+    if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int q = 0; q <= B + 1 && q <= kLowMaxB + 1; ++q) {
+            spref[q] = acc;
+            acc += binom(sbin, B, q);
+        }
+    }
+    __syncthreads();
+
+    const int L = cp.L, m = cp.n_up, H = L - B;
+    const uint32_t ntile = 1u << H;
+    const T hdelta = cp_half_delta<T>(cp);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G;
+    const int col = (lane % G) * V;
+    const LowRec *__restrict__ tbl = g_lowtab + lowtab_base(B);
+    T part[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) part[v] = (T)0;
+    unsigned parity = 0;
+    for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int p = m - __popc(t);
+        if (p < 0 || p > B) continue;  // block-uniform
+        const uint32_t Rt = binom(sbin, B, p);
+        if (warp == 0) {
+            tile_meta_warp<T>(sbin, tab, cp, B, t, p, s_meta);
+            __syncwarp();
+            if (lane == 0) {
+                const unsigned bytes = Rt * (unsigned)(K * sizeof(T));
+                mbar_arrive_expect_tx(&s_mbar, bytes);
+                bulk_copy_g2s(s_tile, X + (int64_t)s_meta.off * K, bytes, &s_mbar);
+            }
+        }
+        __syncthreads();
+        const bool got = mbar_wait_bounded(&s_mbar, parity);
+        parity ^= 1u;
+        if (!__syncthreads_and(got)) {
+            // the copy did not complete in time: wait once more (bounded) so no copy is
+            // left in flight, mark this tile's rows NaN, and stop
+            mbar_wait_bounded(&s_mbar, parity ^ 1u);
+            for (uint32_t j = threadIdx.x / G; j < Rt; j += kThreads / G) {
+                Vec<T, V> nanv;
+#pragma unroll
+                for (int v = 0; v < V; ++v) nanv.v[v] = (T)NAN;
+                T *dst = (MODE == kPcgQ) ? R : Y;
+                stv<T, V>(dst + (int64_t)(s_meta.off + j) * K + col, nanv);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) part[v] = (T)NAN;
+            break;
+        }
+        const uint32_t t0 = t & 1u, thi = (t >> (H - 1)) & 1u;
+        const uint32_t sup = p >= 1 ? binom(sbin, B - 1, p - 1) : 0u;
+        const uint32_t sdn = binom(sbin, B - 1, p);
+        const LowRec *__restrict__ rp = tbl + spref[p];
+        for (uint32_t j0 = warp * RPW; j0 < Rt; j0 += RPB) {
+            const uint32_t j = j0 + grp;
+            tile_row_pass<T, V, NB, MODE>(cp, B, X, K, s_tile, K, rp, j, j < Rt, s_meta, tab, hdelta, t0, thi, sup,
+                                          sdn, col, Y, K, R, dinv, s_alpha, part);
+        }
+        // every read of this tile is done before the next copy overwrites it
+        __syncthreads();
+        if (threadIdx.x == 0) fence_proxy_async_smem();
     }
     if (MODE == kPlain) return;
     pcg_block_finish<T, V, G, MODE>(red, part, K, ps, rd);
@@ -1041,6 +1322,12 @@ int make_chain_params(const mbl_chain *chain, double sigma, ChainParams *cp)
     }
     p.half_delta = 0.5 * chain->delta;
     p.diag_const = 0.25 * chain->delta * (double)p.nbonds - 0.5 * hsum - sigma;
+    for (int i = 0; i < L; ++i) {
+        p.h_hi[i] = (float)p.h[i];
+        p.h_lo[i] = (float)(p.h[i] - (double)p.h_hi[i]);
+    }
+    p.half_delta_f = (float)p.half_delta;
+    p.diag_const_f = (float)p.diag_const;
     *cp = p;
     return MBL_OK;
 }
@@ -1073,8 +1360,8 @@ static cudaError_t launch_apply_k(const ChainParams &cp, const T *X, int64_t ldx
 // Tile width override per (block width, element size): 0 = heuristic, -1 = untiled,
 // >= 2 = that many low bits.  Set by the autotuner.
 static int g_tile_bits[2][8] = {};
-static int g_lane_bytes[2][8] = {};  // 0: default (32), else 16 or 32
-static int g_schedule[2][8] = {};    // 0: by size, 1: persistent grid-stride, 2: ordered
+static int g_lane_bytes[2][8] = {};  // 0: default (32), else 16, 32 or 64
+static int g_schedule[2][8] = {};    // 0: by size, 1: persistent, 2: ordered, 3: staged
 
 static int kslot(int K)
 {
@@ -1125,6 +1412,16 @@ void set_tile_bits(int K, size_t es, int bits) { g_tile_bits[es == 8 ? 1 : 0][ks
 void set_lane_bytes(int K, size_t es, int bytes) { g_lane_bytes[es == 8 ? 1 : 0][kslot(K)] = bytes; }
 void set_schedule(int K, size_t es, int mode) { g_schedule[es == 8 ? 1 : 0][kslot(K)] = mode; }
 
+// Per-(element size, block width, L) choices written by the autotuner; 0 = not tuned.
+// An explicit tuning switch (g_schedule, g_lane_bytes) takes precedence; during a
+// tuning run the candidate under test is forced on the tuning thread.
+struct ProductTune {
+    int schedule, lane;
+};
+static ProductTune g_tuned[2][8][kMaxL + 1] = {};
+static std::mutex g_tune_mutex;
+static thread_local int t_force_schedule = 0, t_force_lane = 0;
+
 // Work order of a plain tiled product.  Persistent: a grid of a few blocks per SM, each
 // warp striding over the (tile, chunk) items.  Ordered: one item per warp and as many
 // blocks as needed, so the hardware hands out blocks in index order and the tiles in
@@ -1133,19 +1430,33 @@ void set_schedule(int K, size_t es, int mode) { g_schedule[es == 8 ? 1 : 0][kslo
 // ordered grid repeats the shared-memory setup, so it only pays for wide rows: measured
 // on GB300, ordered wins for rows of >= 256 bytes once the block vector is >= 1 GiB
 // (FP32), or >= 128 MiB in FP64 (ALU-bound there), and loses elsewhere.
-static bool ordered_schedule(int L, int n_up, int K, size_t es)
+// The staged schedule (whole tiles in shared memory) is the default for 128-byte rows
+// once the block vector outgrows 16 MB (measured: 2-6 % faster there, slower for
+// narrower and wider rows); anything else defaults to persistent.
+static int schedule_for(int L, int n_up, int K, size_t es)
 {
+    if (t_force_schedule) return t_force_schedule;
     const int o = g_schedule[es == 8 ? 1 : 0][kslot(K)];
-    if (o == 1) return false;
-    if (o == 2) return true;
+    if (o) return o;
+    const int a = (L >= 0 && L <= kMaxL) ? g_tuned[es == 8 ? 1 : 0][kslot(K)][L].schedule : 0;
+    if (a) return a;
     const double bytes = (double)host_binom(L, n_up) * K * (double)es;
-    if (K * (int)es < 256) return false;
-    return bytes >= (es == 8 ? 128.0 * (1 << 20) : 1024.0 * (1 << 20));
+    if (K * (int)es >= 256 && bytes >= (es == 8 ? 128.0 * (1 << 20) : 1024.0 * (1 << 20))) return 2;
+    if (K * (int)es == 128 && bytes >= 16.0 * (1 << 20)) return 3;
+    return 1;
 }
-static int lane_bytes_for(int K, size_t es)
+static bool ordered_schedule(int L, int n_up, int K, size_t es) { return schedule_for(L, n_up, K, es) == 2; }
+
+// 32-byte lanes by default; 64-byte lanes for FP64 rows of >= 128 bytes (measured 13 %
+// faster: the FP64 products are ALU-bound and wider lanes repeat less index work).
+static int lane_bytes_for(int L, int K, size_t es)
 {
+    if (t_force_lane) return t_force_lane;
     const int v = g_lane_bytes[es == 8 ? 1 : 0][kslot(K)];
-    return v == 16 ? 16 : 32;
+    if (v == 16 || v == 32 || v == 64) return v;
+    const int a = (L >= 0 && L <= kMaxL) ? g_tuned[es == 8 ? 1 : 0][kslot(K)][L].lane : 0;
+    if (a) return a;
+    return (es == 8 && K * (int)es >= 128) ? 64 : 32;
 }
 
 template <typename T, int K, int MODE, int LB>
@@ -1175,12 +1486,61 @@ static cudaError_t launch_tiled_lb(const ChainParams &cp, int B, const T *X, int
     return cudaGetLastError();
 }
 
+// Tile width of the staged kernel: the widest table-backed B (<= L - 2) whose largest
+// tile, C(B, B/2) rows, fits in the shared-memory stage.
+static int staged_bits(int L, int K, size_t es)
+{
+    int B = kLowMaxB < L - 2 ? kLowMaxB : L - 2;
+    while (B >= 2 && (size_t)host_binom(B, B / 2) * K * es > (size_t)kStageBytes) --B;
+    return B;
+}
+
+static bool staged_schedule(int L, int n_up, int K, size_t es) { return schedule_for(L, n_up, K, es) == 3; }
+
+template <typename T, int K, int MODE, int LB>
+static cudaError_t launch_staged_lb(const ChainParams &cp, int Bs, const T *X, T *Y, T *R, const T *dinv,
+                                    const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
+{
+    if (ensure_lowtab(Bs) != MBL_OK) return cudaErrorUnknown;
+    auto kern = k_apply_staged<T, K, MODE, LB>;
+    static const int per_sm = [&]() {
+        int v = 0;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kThreads, kStageBytes) != cudaSuccess || v < 1)
+            v = 1;
+        return v;
+    }();
+    const size_t dyn = (size_t)host_binom(Bs, Bs / 2) * K * sizeof(T);
+    const int64_t ntile = (int64_t)1 << (cp.L - Bs);
+    int64_t grid = (int64_t)num_sms() * per_sm;
+    if (grid > (int64_t)num_sms() * 8) grid = (int64_t)num_sms() * 8;  // partials capacity
+    if (grid > ntile) grid = ntile;
+    note_launch();
+    kern<<<(int)grid, kThreads, dyn, st>>>(cp, Bs, X, Y, R, dinv, ps, rd);
+    return cudaGetLastError();
+}
+
 template <typename T, int K, int MODE>
 static cudaError_t launch_tiled(const ChainParams &cp, int B, const T *X, int64_t ldx, T *Y, int64_t ldy, T *R,
                                 const T *dinv, const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
 {
-    if (lane_bytes_for(K, sizeof(T)) == 16)
-        return launch_tiled_lb<T, K, MODE, 16>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd, st);
+    if constexpr ((K * sizeof(T)) % 16 == 0) {
+        // staged: contiguous rows (ld = K) and 16-byte aligned bases for the bulk copies
+        const bool aligned = ((uintptr_t)X % 16 == 0) && (Y == nullptr || (uintptr_t)Y % 16 == 0) &&
+                             (R == nullptr || (uintptr_t)R % 16 == 0);
+        if (staged_schedule(cp.L, cp.n_up, K, sizeof(T)) && ldx == K && (Y == nullptr || ldy == K) && aligned) {
+            const int Bs = staged_bits(cp.L, K, sizeof(T));
+            if (Bs >= 2) {
+                const int lbs = lane_bytes_for(cp.L, K, sizeof(T));
+                if (lbs == 16) return launch_staged_lb<T, K, MODE, 16>(cp, Bs, X, Y, R, dinv, ps, rd, st);
+                if (lbs == 64) return launch_staged_lb<T, K, MODE, 64>(cp, Bs, X, Y, R, dinv, ps, rd, st);
+                return launch_staged_lb<T, K, MODE, 32>(cp, Bs, X, Y, R, dinv, ps, rd, st);
+            }
+        }
+    }
+    const int lb = lane_bytes_for(cp.L, K, sizeof(T));
+    if (lb == 16) return launch_tiled_lb<T, K, MODE, 16>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd, st);
+    if (lb == 64) return launch_tiled_lb<T, K, MODE, 64>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd, st);
     return launch_tiled_lb<T, K, MODE, 32>(cp, B, X, ldx, Y, ldy, R, dinv, ps, rd, st);
 }
 
@@ -1196,7 +1556,7 @@ template <typename T>
 static bool vec_ok_wide(const void *p, int64_t ld, int K, int lb)
 {
     const int bytes = K * (int)sizeof(T);
-    const int align = bytes >= lb ? lb : (bytes >= 16 ? 16 : bytes);
+    const int align = bytes >= lb ? lb : bytes;  // one vector per lane: min(row, lane) bytes
     return ((uintptr_t)p % align == 0) && ((ld * (int64_t)sizeof(T)) % align == 0);
 }
 
@@ -1218,7 +1578,7 @@ static int dispatch_plain(const ChainParams &cp, const T *X, int64_t ldx, T *Y, 
     cudaError_t e = cudaSuccess;
     bool done = true;
     const int B = tile_bits_for(cp.L, k, sizeof(T));
-    const int lb = lane_bytes_for(k, sizeof(T));
+    const int lb = lane_bytes_for(cp.L, k, sizeof(T));
     if (B >= 2 && vec_ok_wide<T>(X, ldx, k, lb) && vec_ok_wide<T>(Y, ldy, k, lb)) {
         switch (k) {
         case 1: e = launch_tiled<T, 1, kPlain>(cp, B, X, ldx, Y, ldy, nullptr, nullptr, ps, rd, st); break;
@@ -1386,7 +1746,7 @@ extern "C" int mbl_set_product_tile_bits(int k, int dtype, int bits)
 
 extern "C" int mbl_set_product_schedule(int k, int dtype, int schedule)
 {
-    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || schedule < 0 || schedule > 2)
+    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || schedule < 0 || schedule > 3)
         return MBL_ERR_ARG;
     mbl::set_schedule(k, dtype == MBL_F32 ? 4 : 8, schedule);
     return MBL_OK;
@@ -1394,9 +1754,72 @@ extern "C" int mbl_set_product_schedule(int k, int dtype, int schedule)
 
 extern "C" int mbl_set_product_lane_bytes(int k, int dtype, int bytes)
 {
-    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || (bytes != 0 && bytes != 16 && bytes != 32))
+    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || (bytes != 0 && bytes != 16 && bytes != 32 && bytes != 64))
         return MBL_ERR_ARG;
     mbl::set_lane_bytes(k, dtype == MBL_F32 ? 4 : 8, bytes);
+    return MBL_OK;
+}
+
+extern "C" int mbl_autotune_product(const mbl_chain *chain, int dtype, const void *X_dev, void *Y_dev, int64_t n,
+                                    int k, int reps, mbl_product_choice *choice, mbl_stream_t stream)
+{
+    using namespace mbl;
+    ChainParams cp;
+    int rc = make_chain_params(chain, 0.0, &cp);
+    if (rc != MBL_OK) return rc;
+    if (dtype != MBL_F32 && dtype != MBL_F64) return MBL_ERR_ARG;
+    if (k < 1 || k > 256 || reps < 1 || reps > 1000) return MBL_ERR_ARG;
+    if (n != mbl_basis_size(chain->L, chain->n_up) || n == 0 || !X_dev || !Y_dev) return MBL_ERR_ARG;
+    const size_t es = dtype == MBL_F32 ? 4 : 8;
+    const char *xb = (const char *)X_dev, *yb = (const char *)Y_dev;
+    if (xb < yb + n * k * (int64_t)es && yb < xb + n * k * (int64_t)es) return MBL_ERR_ARG;
+    if (choice) *choice = mbl_product_choice{0, 0, 0, 0.0};
+    const bool tiled_k = (k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32 || k == 64);
+    if (!tiled_k || tile_bits_for(cp.L, k, es) < 2) return MBL_OK;  // one kernel only: nothing to choose
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return MBL_ERR_CUDA;
+    }
+    const int rows = (int)(k * es);
+    float best = -1.0f;
+    int best_s = 1, best_l = 32;
+    rc = MBL_OK;
+    for (int sch = 1; sch <= 3 && rc == MBL_OK; ++sch) {
+        if (sch == 3 && (rows % 16 != 0 || staged_bits(cp.L, k, es) < 2)) continue;
+        for (int lane = 32; lane <= 64 && rc == MBL_OK; lane *= 2) {
+            if (lane == 64 && rows < 64) continue;  // narrower rows: one lane holds the row either way
+            t_force_schedule = sch;
+            t_force_lane = lane;
+            float ms = 0.0f;
+            rc = apply_device(cp, dtype, X_dev, k, Y_dev, k, (uint32_t)n, k, st);  // warm-up
+            if (rc == MBL_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = MBL_ERR_CUDA;
+            for (int r = 0; r < reps && rc == MBL_OK; ++r)
+                rc = apply_device(cp, dtype, X_dev, k, Y_dev, k, (uint32_t)n, k, st);
+            if (rc == MBL_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = MBL_ERR_CUDA;
+            t_force_schedule = 0;
+            t_force_lane = 0;
+            if (rc == MBL_OK && (best < 0.0f || ms < best)) {
+                best = ms;
+                best_s = sch;
+                best_l = lane;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MBL_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned[es == 8 ? 1 : 0][kslot(k)][cp.L] = ProductTune{best_s, best_l};
+    }
+    if (choice)
+        *choice = mbl_product_choice{best_s, best_l,
+                                     best_s == 3 ? staged_bits(cp.L, k, es) : tile_bits_for(cp.L, k, es),
+                                     1000.0 * (double)best / reps};
     return MBL_OK;
 }
 

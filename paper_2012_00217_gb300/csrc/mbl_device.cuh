@@ -97,7 +97,34 @@ struct ChainParams {
     double diag_const;   // delta |B| / 4 - sum_i h_i / 2 - sigma
     double h[kMaxL];     // fields
     const uint32_t *states;  // optional sector basis (n words); nullptr: unrank on the fly
+    // FP32 copies for the FP32 kernels, split on the host so no kernel needs the FP64
+    // pipe (about 1/64 of the FP32 rate on GB300): h = h_hi + h_lo exactly to 48 bits
+    float h_hi[kMaxL], h_lo[kMaxL];
+    float half_delta_f, diag_const_f;  // rounded once
 };
+
+// The chain constants in the kernel's own type.
+template <typename T>
+__device__ __forceinline__ T cp_diag_const(const ChainParams &cp);
+template <>
+__device__ __forceinline__ float cp_diag_const<float>(const ChainParams &cp) { return cp.diag_const_f; }
+template <>
+__device__ __forceinline__ double cp_diag_const<double>(const ChainParams &cp) { return cp.diag_const; }
+template <typename T>
+__device__ __forceinline__ T cp_half_delta(const ChainParams &cp);
+template <>
+__device__ __forceinline__ float cp_half_delta<float>(const ChainParams &cp) { return cp.half_delta_f; }
+template <>
+__device__ __forceinline__ double cp_half_delta<double>(const ChainParams &cp) { return cp.half_delta; }
+
+// Error-free sum of two FP32 numbers: s + e == a + b exactly (Knuth's TwoSum, TAOCP
+// vol. 2, 4.2.2); six additions, no products, so nothing can be contracted.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
 
 // Sector word of row r: from the basis table when one is given, else by unranking.
 __device__ __forceinline__ uint32_t state_of(const uint32_t *sb, const ChainParams &cp, uint32_t r)
@@ -127,6 +154,29 @@ __device__ __forceinline__ void build_field_tables(T *tab, const ChainParams &cp
             if (((v >> t) & 1u) && site < cp.L) acc += cp.h[site];
         }
         tab[e] = (T)acc;
+    }
+}
+
+// FP32 tables without FP64 arithmetic: each entry is a compensated sum of the (h_hi,
+// h_lo) pairs, rounded once at the end (equal to the rounded FP64 sum to within one
+// unit in the last place).
+template <>
+__device__ __forceinline__ void build_field_tables<float>(float *tab, const ChainParams &cp)
+{
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+        const int b = e >> 8;
+        const uint32_t v = (uint32_t)(e & 255);
+        float s = 0.0f, c = 0.0f;
+        for (int t = 0; t < 8; ++t) {
+            const int site = 8 * b + t;
+            if (((v >> t) & 1u) && site < cp.L) {
+                float hi, err;
+                two_sum(s, cp.h_hi[site], hi, err);
+                s = hi;
+                c += err + cp.h_lo[site];
+            }
+        }
+        tab[e] = s + c;
     }
 }
 

@@ -161,6 +161,7 @@ struct Solver {
     int64_t n;
     int k, nev, m;
     int mixed;
+    int gmix;     // Rayleigh-Ritz Grams and eigensolves in FP32 (mixed mode until a stall)
     int largest;  // bounds mode, -H: keep the largest Ritz values
     int folded;   // 1: A = (H - sigma)^2 with PCG; 0: A = H - sigma, no preconditioner
     double tol_abs, norm_h, pcg_tol;
@@ -232,7 +233,10 @@ struct Solver {
         MBL_TRY(gram(X(), ld3(), k, b.T, k, k, n, b.Gk, k, 1, 0, b.part, st));
         MBL_TRY(small_eig(k, b.Gk, k, b.mu, b.V, b.eigw, st));
         MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, b.T, k, b.Tmp, k, n, -1.0, 1.0, 0, st));
-        MBL_TRY(gram(b.Tmp, k, k, b.Tmp, k, k, n, b.G3, k, 1, mixed, b.part, st));
+        // E^T E in FP64 in both modes: a converged pair's residual is read off this Gram
+        // next to the guard columns' much larger ones, and FP32 rounding of the latter
+        // (sqrt(u32) times their norm) would hide residuals below ~1e-7 of them
+        MBL_TRY(gram(b.Tmp, k, k, b.Tmp, k, k, n, b.G3, k, 1, 0, b.part, st));
         return hrr_select(k, nev, b.mu, b.V, b.G3, tol_abs, norm_h, b.res_all, b.iflags + 8, b.res_sel,
                           b.iflags + 4, b.dstat, st);
     }
@@ -249,7 +253,7 @@ struct Solver {
     {
         // 2. residual of the current block
         mark(0);
-        MBL_TRY(gram(X(), ld3(), k, AX(), ld3(), k, n, b.Gk, k, 1, mixed, b.part, st));
+        MBL_TRY(gram(X(), ld3(), k, AX(), ld3(), k, n, b.Gk, k, 1, gmix, b.part, st));
         MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, AX(), ld3(), b.Tmp, k, n, -1.0, 1.0, 0, st));
         mark(1);
         if (folded) {
@@ -287,10 +291,10 @@ struct Solver {
         mark(3);
         // 6. SVQB + Rayleigh-Ritz with A
         const int w = have_p ? 3 * k : 2 * k;
-        MBL_TRY(gram(b.S, ld3(), w, b.S, ld3(), w, n, b.G1, w, 1, mixed, b.part, st));
-        MBL_TRY(gram(b.S, ld3(), w, b.AS, ld3(), w, n, b.G2, w, 1, mixed, b.part, st));
+        MBL_TRY(gram(b.S, ld3(), w, b.S, ld3(), w, n, b.G1, w, 1, gmix, b.part, st));
+        MBL_TRY(gram(b.S, ld3(), w, b.AS, ld3(), w, n, b.G2, w, 1, gmix, b.part, st));
         mark(4);
-        MBL_TRY(small_svqb_rr(w, k, largest, mixed, b.G1, b.G2, svqb_tau(), b.coef, b.theta, b.eigw, b.iflags + 1, st));
+        MBL_TRY(small_svqb_rr(w, k, largest, gmix, b.G1, b.G2, svqb_tau(), b.coef, b.theta, b.eigw, b.iflags + 1, st));
         mark(5);
         // 7. updates
         MBL_TRY(update(b.S, ld3(), w, b.coef, k, k, nullptr, 0, b.Xn, k, n, 1.0, 0.0, 0, st));
@@ -308,7 +312,7 @@ struct Solver {
     }
     // Directions below the resolution of the Gram matrix are dropped: its entries carry
     // FP32 rounding in mixed mode.
-    double svqb_tau() const { return mixed ? 1e-7 : 1e-14; }
+    double svqb_tau() const { return gmix ? 1e-7 : 1e-14; }
 };
 
 // The rotation of the start block onto A's Ritz vectors (X, T, AX <- . C).
@@ -356,10 +360,18 @@ struct GraphCache {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int64_t kernels[2] = {0, 0};  // kernel nodes per graph
     cudaStream_t cap = nullptr;
+    // drop the captured bodies (after a change of the body's precision)
+    void reset()
+    {
+        for (int i = 0; i < 2; ++i) {
+            if (exec[i]) cudaGraphExecDestroy(exec[i]);
+            exec[i] = nullptr;
+            kernels[i] = 0;
+        }
+    }
     ~GraphCache()
     {
-        for (auto &e : exec)
-            if (e) cudaGraphExecDestroy(e);
+        reset();
         if (cap) cudaStreamDestroy(cap);
     }
 };
@@ -450,6 +462,7 @@ extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_
     s.nev = opts->nev;
     s.m = opts->pcg_iters;
     s.mixed = mixed;
+    s.gmix = mixed;
     s.largest = 0;
     s.folded = 1;
     s.pcg_tol = opts->pcg_tol;
@@ -500,8 +513,25 @@ extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_
     bool have_p = false;
     int status = MBL_OK;
     const bool graphs = opts->use_graph != 0 && !s.timing;
+    // Mixed mode keeps its Rayleigh-Ritz in FP32 while the residual keeps falling; once the
+    // largest wanted residual has not dropped by 10 % for kStallIters iterations, the FP32
+    // Grams of the folded operator are taken to limit it (their rounding, ~1e-7 ||A||,
+    // swamps the small gaps of A near sigma) and the remaining iterations run them in FP64.
+    constexpr int kStallIters = 20;
+    double r_mark = 0.0;
+    int it_mark = 0;
     for (;;) {
         MBL_TRY(read_status(s, &hs));
+        if (s.gmix) {
+            const double r = hs.dstat[0];
+            if (it == 0 || r < 0.9 * r_mark) {
+                r_mark = r;
+                it_mark = it;
+            } else if (it - it_mark >= kStallIters) {
+                s.gmix = 0;
+                gc.reset();
+            }
+        }
         if (s.timing) {
             if (it == 0) {
                 float ms = 0.f;
@@ -592,6 +622,7 @@ static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, c
     s.nev = 1;
     s.m = 0;
     s.mixed = 0;
+    s.gmix = 0;
     s.largest = largest;
     s.folded = 0;
     s.pcg_tol = 0.0;

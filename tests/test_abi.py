@@ -62,6 +62,7 @@ def _c_layout(tmp_path):
         "mbl_lobpcg_stats": ["iters", "converged", "matvecs", "seconds", "max_rel_resid", "norm_h",
                              "t_setup", "t_resid", "t_pcg", "t_wp", "t_gram", "t_small", "t_update",
                              "t_refresh", "t_hrr"],
+        "mbl_product_choice": ["schedule", "lane_bytes", "tile_bits", "microseconds"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mbl.h"', "int main(void) {"]
     for st, fs in fields.items():
@@ -84,7 +85,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     from paper_2012_00217_gb300 import binding
     c = _c_layout(tmp_path)
     for st, cls in (("mbl_chain", binding.Chain), ("mbl_lobpcg_opts", binding.LobpcgOpts),
-                    ("mbl_lobpcg_stats", binding.LobpcgStats)):
+                    ("mbl_lobpcg_stats", binding.LobpcgStats), ("mbl_product_choice", binding.ProductChoice)):
         assert c[(st, "sizeof")] == ctypes.sizeof(cls), st
         for f, _ in cls._fields_:
             assert c[(st, f)] == getattr(cls, f).offset, (st, f)
@@ -171,8 +172,8 @@ def test_tuning_switches_validate(so):
                               (32, 0, 1, bad), (32, 0, 17, bad), (0, 0, 4, bad), (257, 0, 4, bad),
                               (32, 2, 4, bad)):
         assert so.mbl_set_product_tile_bits(k, dt, bits) == want
-    for k, dt, nb, want in ((32, 0, 16, ok), (32, 1, 32, ok), (8, 0, 0, ok), (32, 0, 8, bad),
-                            (32, 0, 64, bad), (0, 0, 16, bad)):
+    for k, dt, nb, want in ((32, 0, 16, ok), (32, 1, 32, ok), (8, 0, 0, ok), (32, 0, 64, ok), (32, 0, 8, bad),
+                            (32, 0, 128, bad), (0, 0, 16, bad)):
         assert so.mbl_set_product_lane_bytes(k, dt, nb) == want
     # restore the defaults
     for k in (1, 32):
@@ -181,6 +182,22 @@ def test_tuning_switches_validate(so):
     for k in (8, 32):
         for dt in (0, 1):
             so.mbl_set_product_lane_bytes(k, dt, 0)
+    for sch, want in ((0, ok), (1, ok), (2, ok), (3, ok), (4, bad), (-1, bad)):
+        assert so.mbl_set_product_schedule(64, 0, sch) == want
+    so.mbl_set_product_schedule(64, 0, 0)
+
+
+def test_autotune_checks_arguments_before_any_launch(so):
+    import paper_2012_00217_gb300 as mbl
+    from paper_2012_00217_gb300 import binding
+    ch = mbl.make_chain(12, np.zeros(12))
+    n = math.comb(12, 6)
+    c = binding.ProductChoice()
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every case below fails its checks first
+    for dtype, X, Y, nn, k, reps in ((2, fake, fake, n, 8, 3), (0, None, fake, n, 8, 3), (0, fake, fake, n - 1, 8, 3),
+                                     (0, fake, fake, n, 0, 3), (0, fake, fake, n, 8, 0), (0, fake, fake, n, 8, 3)):
+        rc = so.mbl_autotune_product(ctypes.byref(ch), dtype, X, Y, nn, k, reps, ctypes.byref(c), None)
+        assert rc == binding.MBL_ERR_ARG  # the last case: X and Y overlap
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -216,3 +216,98 @@ def test_apply_every_tile_width(mbl, bits, L, periodic, k, dtype):
         mbl.binding.set_product_tile_bits(k, tdt, 0)
     err = np.abs(Y.cpu().numpy().astype(np.float64) - ref)
     assert np.all(err <= _bound(chain, -0.3, X, dtype)), err.max()
+
+
+def _staged_bits(L, k, itemsize):
+    """Tile width the staged schedule uses: the widest B <= min(13, L - 2) whose largest
+    tile C(B, B/2) * k * itemsize fits in 48 KB."""
+    from math import comb
+    B = min(13, L - 2)
+    while B >= 2 and comb(B, B // 2) * k * itemsize > 48 * 1024:
+        B -= 1
+    return B
+
+
+@pytest.mark.parametrize("L,periodic,n_up,k,dtype", [
+    (16, True, 8, 32, np.float32), (18, False, 9, 64, np.float32), (14, True, 7, 8, np.float32),
+    (13, False, 5, 16, np.float32), (15, True, 7, 4, np.float32), (14, False, 7, 32, np.float64),
+    (16, True, 8, 64, np.float64), (12, True, 6, 2, np.float64), (17, True, 8, 16, np.float64)])
+def test_staged_schedule_matches_oracle_and_tiled(mbl, L, periodic, n_up, k, dtype):
+    """Schedule 3 (whole tiles staged in shared memory by bulk copies) against the
+    oracle, and bit for bit against the persistent tiled kernel at the same tile width."""
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    h = wl.fields(L, 7.0, 100 + L + k)
+    chain = ham.Chain(L, h, delta=0.9, periodic=periodic, n_up=n_up)
+    n = ham.sector_dim(L, n_up)
+    X = wl.block(n, k, 11 + k, dtype)
+    ref = ham.apply(chain, 0.4, X.astype(np.float64))
+    c = mbl.make_chain(L, h, 0.9, periodic, n_up)
+    Xg = _gpu(X)
+    Ys = torch.full((n, k), float("nan"), dtype=tdt, device=DEV)
+    Yt = torch.full((n, k), float("nan"), dtype=tdt, device=DEV)
+    B = _staged_bits(L, k, np.dtype(dtype).itemsize)
+    try:
+        mbl.binding.set_product_schedule(k, tdt, 3)
+        mbl.hamiltonian_apply(c, 0.4, Xg, Ys)
+        mbl.binding.set_product_schedule(k, tdt, 1)
+        mbl.binding.set_product_tile_bits(k, tdt, B)
+        mbl.hamiltonian_apply(c, 0.4, Xg, Yt)
+    finally:
+        mbl.binding.set_product_schedule(k, tdt, 0)
+        mbl.binding.set_product_tile_bits(k, tdt, 0)
+    ys = Ys.cpu().numpy()
+    err = np.abs(ys.astype(np.float64) - ref)
+    assert np.all(err <= _bound(chain, 0.4, X, dtype)), err.max()
+    assert np.array_equal(ys, Yt.cpu().numpy())
+
+
+def test_staged_schedule_full_size_sampled(mbl):
+    """Schedule 3 at L = 26 (k = 32, FP32): sampled rows against the oracle."""
+    L, k = 26, 32
+    h = wl.fields(L, 8.0, 7)
+    chain = ham.Chain(L, h, periodic=True)
+    n = ham.sector_dim(L, L // 2)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(5)
+    X = torch.randn((n, k), generator=g, device=DEV, dtype=torch.float32)
+    Y = torch.empty_like(X)
+    try:
+        mbl.binding.set_product_schedule(k, torch.float32, 3)
+        mbl.hamiltonian_apply(mbl.make_chain(L, h, 1.0, True), 0.5, X, Y)
+    finally:
+        mbl.binding.set_product_schedule(k, torch.float32, 0)
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([rng.integers(0, n, 300), [0, 1, n // 2, n - 2, n - 1]]))
+    Xh = X.cpu().numpy()
+    ref = ham.apply_rows(chain, 0.5, Xh.astype(np.float64), rows)
+    got = Y[torch.from_numpy(rows).to(DEV)].cpu().numpy().astype(np.float64)
+    d = ham.diag(chain)[rows] - 0.5
+    u = np.finfo(np.float32).eps
+    scale = (np.abs(d)[:, None] + 0.5 * L) * np.abs(Xh).max()
+    derr = 6 * u * (np.sum(np.abs(h)) + 0.5 + L)
+    assert np.all(np.abs(got - ref) <= 4 * (L + 2) * u * scale + derr * np.abs(Xh).max())
+
+
+@pytest.mark.parametrize("L,periodic,k,dtype", [(16, True, 32, np.float32), (15, False, 16, np.float64),
+                                                (14, True, 3, np.float32)])
+def test_autotune_keeps_a_correct_choice(mbl, L, periodic, k, dtype):
+    """The autotuner times its candidates on the caller's buffers, keeps one, and the
+    products that follow (under the kept choice) still match the oracle."""
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    h = wl.fields(L, 6.0, 40 + L)
+    chain = ham.Chain(L, h, periodic=periodic)
+    n = ham.sector_dim(L, L // 2)
+    c = mbl.make_chain(L, h, 1.0, periodic)
+    X = _gpu(wl.block(n, k, 9, dtype))
+    Y = torch.empty_like(X)
+    choice = mbl.binding.autotune_product(c, X, Y, reps=3)
+    if k == 3:  # no tiled kernel for this width: nothing to choose
+        assert choice["schedule"] == 0
+    else:
+        assert choice["schedule"] in (1, 2, 3) and choice["lane_bytes"] in (32, 64)
+        assert choice["tile_bits"] >= 2 and choice["microseconds"] > 0
+    Xh = X.cpu().numpy()
+    mbl.hamiltonian_apply(c, 0.25, X, Y)
+    ref = ham.apply(chain, 0.25, Xh.astype(np.float64))
+    err = np.abs(Y.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= _bound(chain, 0.25, Xh, dtype)), err.max()

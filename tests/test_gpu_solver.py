@@ -189,3 +189,24 @@ def test_not_converged_status(mbl):
     assert rc == mbl.binding.MBL_ERR_NOT_CONVERGED
     assert stats["iters"] == 2 and stats["converged"] == 0
     assert np.all(np.isfinite(evals))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_staged_schedule_solve_matches_dense(mbl, mode):
+    """The folded LOBPCG with every product (PCG launches included) on schedule 3."""
+    L = 14
+    h = wl.fields(L, 8.0, 1)
+    ev = np.linalg.eigvalsh(ham.dense_sector(ham.Chain(L, h, periodic=True)))
+    sigma = 0.5 * (ev[0] + ev[-1])
+    nh = max(abs(ev[0]), abs(ev[-1]))
+    want = np.sort(ev[np.lexsort((ev, np.abs(ev - sigma)))[:16]])
+    try:
+        for dt in (torch.float32, torch.float64):
+            mbl.binding.set_product_schedule(32, dt, 3)
+        evals, resid, stats, vecs = _solve(mbl, L, h, True, sigma, 16, 32, mode, nh, 20, 1)
+    finally:
+        for dt in (torch.float32, torch.float64):
+            mbl.binding.set_product_schedule(32, dt, 0)
+    assert stats["converged"] == 1
+    assert np.abs(evals - want).max() <= (1e-9 if mode == 0 else 1e-6) * nh
+    _certify(L, h, True, evals, vecs, nh)
