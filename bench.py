@@ -342,6 +342,41 @@ def batched_sample(torch, mbl, dev, nstreams=16):
                 sample="per W in {2,4,8}: seeds 0-9 (L=16), 256-258 (L=14), 320-322 (L=18), open chains")
 
 
+def config_l26_iterations(torch, mbl, dev, iters=2):
+    """The L = 26 periodic workload (n = 10,400,600, nev = 32, k = 64, mixed): spectrum
+    bounds, then the folded LOBPCG stopped after `iters` iterations (a converged solve
+    at this size needs far more PCG steps than a bench run can hold); reports the time
+    per LOBPCG iteration from the per-phase CUDA events and the residual reached."""
+    cfg = wl.SOLVE_L26
+    L, k, nev = cfg["L"], cfg["k"], cfg["nev"]
+    h = wl.fields(L, cfg["W"], cfg["seed"])
+    chain = mbl.make_chain(L, h, cfg["delta"], cfg["periodic"])
+    n = mbl.basis_size(L, L // 2)
+    opts = mbl.make_opts(nev, k, tol=1e-8, max_iter=iters, pcg_iters=PCG_ITERS, mode=mbl.MODE_MIXED,
+                         use_graph=0, timing=1)
+    ws_bytes = max(mbl.lobpcg_workspace_size(chain, opts), mbl.bounds_workspace_size(chain, 4))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    X0 = torch.from_numpy(wl.initial_block(n, k, cfg["seed"])).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(cfg["seed"] + 100)
+    Xb = torch.randn((n, 4), generator=g, device=dev, dtype=torch.float64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    emin, emax, bit = mbl.spectrum_bounds(chain, Xb, ws, tol=BOUNDS_TOL, max_iter=1000)
+    torch.cuda.synchronize()
+    t_bounds = time.perf_counter() - t0
+    opts.norm_h = max(abs(emin), abs(emax))
+    evals, resid, st, rc = mbl.lobpcg_solve(chain, 0.5 * (emin + emax), opts, X0, ws, allow_not_converged=True)
+    per_iter = sum(v for kk, v in st.items() if kk.startswith("t_") and kk != "t_setup") / max(1, st["iters"])
+    del ws, X0, Xb
+    torch.cuda.empty_cache()
+    return dict(workload=cfg["name"], n=n, nev=nev, k=k, pcg_iters=PCG_ITERS, iterations=st["iters"],
+                seconds_per_iteration=per_iter, setup_s=st["t_setup"], bounds_s=t_bounds, bounds_iters=bit,
+                max_rel_resid_reached=st["max_rel_resid"], workspace_gb=ws_bytes / 1e9,
+                phases_s={kk: v for kk, v in st.items() if kk.startswith("t_")},
+                note="stopped after %d iterations: per-iteration time only, not a converged solve" % iters)
+
+
 def cpu_baseline(s, gpu_iters, budget_s=20.0):
     """The oracle as it stands on this host: one LOBPCG iteration of the same workload
     (bounds + setup + 1 iteration with the same PCG count), extrapolated to the GPU's
@@ -395,7 +430,8 @@ def run_reference(args):
 def run_profile(args):
     """Small fixed workloads for ncu: 'product' launches the L = 20 (k = 32) and L = 26
     (k = 64) FP32 block products three times each; 'pcg' runs a 3-iteration solve;
-    'bounds' runs the spectrum bounds of the bench workload once."""
+    'bounds' runs the spectrum bounds of the bench workload once; 'gram' runs the
+    tensor-core Gram at n = 184,756 (96 x 96) and n = 705,432 (192 x 192) twice each."""
     import torch
     import paper_2012_00217_gb300 as mbl
     dev = torch.device("cuda:0")
@@ -413,6 +449,17 @@ def run_profile(args):
                 mbl.hamiltonian_apply(chain, 0.0, X, Y)
             torch.cuda.synchronize()
             del X, Y
+    elif args.profile == "gram":
+        # the Rayleigh-Ritz Grams S^T S of the L = 20 solve (n = 184,756, 96 x 96) and of
+        # an L = 22 block of width 192, on the tensor cores, twice each
+        for n, w in ((184756, 96), (705432, 192)):
+            g = torch.Generator(device=dev)
+            g.manual_seed(w)
+            A = torch.randn((n, w), generator=g, device=dev, dtype=torch.float64)
+            for _ in range(2):
+                mbl.binding.gram(A, A, "f32", 2)
+            torch.cuda.synchronize()
+            del A
     elif args.profile == "bounds":
         s = _setup(torch, mbl, dev)
         step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
@@ -439,7 +486,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the sweep, the batch and the CPU baseline")
-    ap.add_argument("--profile", choices=["product", "pcg", "bounds"], default=None,
+    ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
                          "FP32) or a 3-iteration solve, for an ncu capture")
     args = ap.parse_args()
@@ -511,6 +558,7 @@ def main():
     big = [r for r in sweep if r["L"] == 26 and r["k"] == 64 and r["dtype"] == "f32"]
     head = big[0] if big else None
     batch = None if args.quick else batched_sample(torch, mbl, dev)
+    l26 = None if args.quick else config_l26_iterations(torch, mbl, dev)
 
     line = {
         "metric": METRIC,
@@ -550,6 +598,7 @@ def main():
         "solve_phases_s": phases,
         "bounds_s": t_b,
         "batched": batch,
+        "l26_periodic_k64": l26,
         "matvec_sweep": sweep,
         "clocks": ck,
     }

@@ -152,6 +152,28 @@ typedef struct {
 int mbl_autotune_product(const mbl_chain *chain, int dtype, const void *X_dev, void *Y_dev, int64_t n, int k,
                          int reps, mbl_product_choice *choice, mbl_stream_t stream);
 
+/* Tuning: engine of the FP32 Gram matrices of mixed mode (S^T S, S^T A S, X^T A X; the
+ * tall-skinny contraction of the Rayleigh-Ritz step, Sec. 3.2): 0 = default (tensor cores
+ * when both sides are >= 96, else CUDA cores), 1 = CUDA cores (FP32 FMA), 2 = tensor
+ * cores whenever the shape fits (tcgen05.mma kind::tf32 with FP32
+ * accumulators in tensor memory; each FP32 operand split into two TF32 parts, three
+ * products, error of the order of FP32 rounding; for Grams up to 256 x 256).  Applies to
+ * later solves in this process.  Returns MBL_ERR_ARG for any other value. */
+int mbl_set_gram_engine(int engine);
+
+/* The tall-skinny Gram of the Rayleigh-Ritz step (Sec. 3.2), on its own: C = A^T B for
+ * FP64 device blocks A (n x p, row-major, lda >= p) and B (n x q, ldb >= q), 1 <= p, q
+ * <= 256, into C (p x q, row-major, ldc >= q, FP64 device memory).  precision MBL_F64:
+ * FP64 arithmetic (CUDA cores); MBL_F32: inputs rounded to FP32, products accumulated in
+ * FP32 per slab of rows, slabs summed in FP64 in a fixed order, on the engine given
+ * (0: the process-wide choice of mbl_set_gram_engine, 1: CUDA cores, 2: tensor cores;
+ * 2 with MBL_F64 is MBL_ERR_ARG).  Workspace: mbl_gram_workspace_size bytes of device memory.
+ * Deterministic for a given engine. */
+int mbl_gram_workspace_size(int64_t n, int p, int q, size_t *bytes);
+int mbl_gram(const double *A_dev, int64_t lda, int p, const double *B_dev, int64_t ldb, int q, int64_t n,
+             double *C_dev, int64_t ldc, int precision, int engine, void *workspace_dev, size_t workspace_bytes,
+             mbl_stream_t stream);
+
 /* ---- folded-spectrum LOBPCG (Sec. 3.2, Sec. 6.2) ---------------------------------- */
 
 typedef struct {

@@ -33,7 +33,8 @@ EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis
             "mbl_bounds_workspace_size", "mbl_spectrum_bounds", "mbl_lobpcg_solve_noalloc",
             "mbl_set_product_tile_bits", "mbl_set_product_lane_bytes", "mbl_batched_workspace_size",
             "mbl_lobpcg_solve_batched", "mbl_kernel_launch_count",
-            "mbl_set_product_schedule", "mbl_autotune_product")
+            "mbl_set_product_schedule", "mbl_autotune_product", "mbl_set_gram_engine",
+            "mbl_gram_workspace_size", "mbl_gram")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -101,6 +102,12 @@ def lib():
     so.mbl_set_product_lane_bytes.argtypes = [i32, i32, i32]
     so.mbl_set_product_schedule.restype = i32
     so.mbl_set_product_schedule.argtypes = [i32, i32, i32]
+    so.mbl_set_gram_engine.restype = i32
+    so.mbl_set_gram_engine.argtypes = [i32]
+    so.mbl_gram_workspace_size.restype = i32
+    so.mbl_gram_workspace_size.argtypes = [i64, i32, i32, ctypes.POINTER(sz)]
+    so.mbl_gram.restype = i32
+    so.mbl_gram.argtypes = [p, i64, i32, p, i64, i32, i64, p, i64, i32, i32, p, sz, p]
     so.mbl_autotune_product.restype = i32
     so.mbl_autotune_product.argtypes = [pch, i32, p, p, i64, i32, i32, ctypes.POINTER(ProductChoice), p]
     so.mbl_set_product_tile_bits.restype = i32
@@ -225,6 +232,30 @@ def set_product_schedule(k, dtype, schedule):
     torch = _torch()
     dt = MBL_F32 if dtype == torch.float32 else MBL_F64
     _check(lib().mbl_set_product_schedule(int(k), dt, int(schedule)), "mbl_set_product_schedule")
+
+
+def set_gram_engine(engine):
+    """mbl_set_gram_engine: 0 default, 1 CUDA cores, 2 tensor cores (tcgen05 TF32 x3)."""
+    _check(lib().mbl_set_gram_engine(int(engine)), "mbl_set_gram_engine")
+
+
+def gram(A, B, precision="f32", engine=0):
+    """mbl_gram: C = A^T B for contiguous FP64 CUDA tensors A (n x p), B (n x q); returns
+    C as a new p x q FP64 CUDA tensor."""
+    torch = _torch()
+    if A.dim() != 2 or B.dim() != 2 or A.shape[0] != B.shape[0] or not (A.is_contiguous() and B.is_contiguous()):
+        raise ValueError("A (n x p), B (n x q): contiguous, same n")
+    n, p_ = A.shape
+    q = B.shape[1]
+    sz = ctypes.c_size_t(0)
+    _check(lib().mbl_gram_workspace_size(int(n), int(p_), int(q), ctypes.byref(sz)), "mbl_gram_workspace_size")
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=A.device)
+    C = torch.empty((p_, q), dtype=torch.float64, device=A.device)
+    prec = MBL_F32 if precision == "f32" else MBL_F64
+    _check(lib().mbl_gram(_dev(A, torch.float64, "A"), int(p_), int(p_), _dev(B, torch.float64, "B"), int(q), int(q),
+                          int(n), _dev(C, torch.float64, "C"), int(q), prec, int(engine), _dev(ws, torch.uint8, "ws"),
+                          ws.numel(), _stream_ptr(A)), "mbl_gram")
+    return C
 
 
 def autotune_product(chain, X, Y, reps=5):

@@ -79,21 +79,40 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double *__restrict__
         }
 }
 
-// C[i][j] (ldc) = sum over slabs, in slab order, of part[slab][i][j]; optionally the
-// symmetric part (C + C^T)/2 when p == q and sym != 0.
+// C[i][j] (ldc) = sum over slabs of part[slab][i][j]; optionally the symmetric part
+// (C + C^T)/2 when p == q and sym != 0.  A block takes 32 consecutive outputs; its 8
+// warps split the slabs (warp g sums slabs g, g + 8, ...), and one thread per output
+// adds the 8 group sums in group order, so the result is the same on every run.
+constexpr int kRedGroups = 8;
+
 __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ part, int nslab, int p, int q,
                                                      double *__restrict__ C, int64_t ldc, int sym)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= p * q) return;
-    const int i = e / q, j = e % q;
+    __shared__ double s_sum[kRedGroups][32], s_tr[kRedGroups][32];
+    const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + o;
+    const int pq = p * q;
     double s = 0.0, t = 0.0;
-    for (int b = 0; b < nslab; ++b) s += part[(int64_t)b * p * q + e];
-    if (sym) {
-        for (int b = 0; b < nslab; ++b) t += part[(int64_t)b * p * q + (int64_t)j * q + i];
-        s = 0.5 * (s + t);
+    if (e < pq) {
+        const int i = e / q, j = e % q;
+        const int64_t et = (int64_t)j * q + i;
+        for (int b = g; b < nslab; b += kRedGroups) {
+            s += part[(int64_t)b * pq + e];
+            if (sym) t += part[(int64_t)b * pq + et];
+        }
     }
-    C[(int64_t)i * ldc + j] = s;
+    s_sum[g][o] = s;
+    s_tr[g][o] = t;
+    __syncthreads();
+    if (g == 0 && e < pq) {
+        double a = 0.0, c = 0.0;
+        for (int h = 0; h < kRedGroups; ++h) {
+            a += s_sum[h][o];
+            c += s_tr[h][o];
+        }
+        const int i = e / q, j = e % q;
+        C[(int64_t)i * ldc + j] = sym ? 0.5 * (a + c) : a;
+    }
 }
 
 // Output tile edge: 64 when both sizes are multiples of 64, 16 for tiny outputs, else 32.
@@ -115,7 +134,28 @@ static int gram_slabs(int64_t n, int p, int q)
     return want;
 }
 
-size_t gram_partial_doubles(int64_t n, int p, int q) { return (size_t)gram_slabs(n, p, q) * p * q; }
+size_t gram_partial_doubles(int64_t n, int p, int q)
+{
+    const size_t cuda = (size_t)gram_slabs(n, p, q), tc = gram_tc_supported(p, q) ? (size_t)gram_tc_slabs(n, p) : 0;
+    return (cuda > tc ? cuda : tc) * p * q;
+}
+
+static int g_gram_engine = 0;
+static thread_local int t_gram_engine = 0;  // per-call choice (mbl_gram), overrides the switch
+void set_gram_engine(int engine) { g_gram_engine = engine; }
+void set_gram_engine_local(int engine) { t_gram_engine = engine; }
+
+// FP32 Grams go to the tensor cores when selected and the shape fits (p, q <= 256).  By
+// default only when both sides are >= 96: the 128-row accumulator tile is then mostly
+// used (measured at n = 184,756: 96 x 96 in 255 us against 609 us on the CUDA cores,
+// 192 x 192 at n = 10.4 M in 35 ms against 70 ms; 64 x 64 and smaller are faster on the
+// CUDA cores).
+static bool use_tensor_cores(int p, int q)
+{
+    const int e = t_gram_engine ? t_gram_engine : g_gram_engine;
+    if (e == 1 || !gram_tc_supported(p, q)) return false;
+    return e == 2 || (p >= 96 && q >= 96);
+}
 
 template <typename CT, int TS>
 static void launch_gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n,
@@ -129,6 +169,14 @@ static void launch_gram(const double *A, int64_t lda, int p, const double *B, in
 int gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n, double *C,
          int64_t ldc, int sym, int compute_f32, double *part, cudaStream_t st)
 {
+    if (compute_f32 && use_tensor_cores(p, q)) {
+        const int nslab = gram_tc_slabs(n, p);
+        const int rc = gram_tc_partial(A, lda, p, B, ldb, q, n, nslab, part, st);
+        if (rc != MBL_OK) return rc;
+        note_launch();
+        k_gram_reduce<<<(p * q + 31) / 32, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym);
+        return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+    }
     const int nslab = gram_slabs(n, p, q);
     const int64_t rps = (n + nslab - 1) / nslab;
     const int ts = gram_tile(p, q);
@@ -142,7 +190,7 @@ int gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int 
         else launch_gram<double, 16>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
     }
     note_launch();
-    k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym);
+    k_gram_reduce<<<(p * q + 31) / 32, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
 

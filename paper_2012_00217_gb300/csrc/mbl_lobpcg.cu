@@ -871,3 +871,35 @@ extern "C" int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, cons
 }
 
 extern "C" int64_t mbl_kernel_launch_count(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
+
+extern "C" int mbl_set_gram_engine(int engine)
+{
+    if (engine < 0 || engine > 2) return MBL_ERR_ARG;
+    mbl::set_gram_engine(engine);
+    return MBL_OK;
+}
+
+extern "C" int mbl_gram_workspace_size(int64_t n, int p, int q, size_t *bytes)
+{
+    if (!bytes || n < 1 || n > ((int64_t)1 << 31) || p < 1 || q < 1 || p > 256 || q > 256) return MBL_ERR_ARG;
+    *bytes = mbl::gram_partial_doubles(n, p, q) * sizeof(double) + 256;
+    return MBL_OK;
+}
+
+extern "C" int mbl_gram(const double *A_dev, int64_t lda, int p, const double *B_dev, int64_t ldb, int q, int64_t n,
+                        double *C_dev, int64_t ldc, int precision, int engine, void *workspace_dev,
+                        size_t workspace_bytes, mbl_stream_t stream)
+{
+    size_t need = 0;
+    if (mbl_gram_workspace_size(n, p, q, &need) != MBL_OK) return MBL_ERR_ARG;
+    if (!A_dev || !B_dev || !C_dev || !workspace_dev || lda < p || ldb < q || ldc < q) return MBL_ERR_ARG;
+    if ((precision != MBL_F32 && precision != MBL_F64) || engine < 0 || engine > 2) return MBL_ERR_ARG;
+    if (precision == MBL_F64 && engine == 2) return MBL_ERR_ARG;  // the tensor-core path is FP32-accurate
+    if (workspace_bytes < need) return MBL_ERR_WORKSPACE;
+    double *part = (double *)(((uintptr_t)workspace_dev + 255) & ~(uintptr_t)255);
+    const int f32 = precision == MBL_F32;
+    mbl::set_gram_engine_local(f32 ? engine : 1);
+    const int rc = mbl::gram(A_dev, lda, p, B_dev, ldb, q, n, C_dev, ldc, 0, f32, part, (cudaStream_t)stream);
+    mbl::set_gram_engine_local(0);
+    return rc;
+}

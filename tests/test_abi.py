@@ -185,6 +185,9 @@ def test_tuning_switches_validate(so):
     for sch, want in ((0, ok), (1, ok), (2, ok), (3, ok), (4, bad), (-1, bad)):
         assert so.mbl_set_product_schedule(64, 0, sch) == want
     so.mbl_set_product_schedule(64, 0, 0)
+    for eng, want in ((0, ok), (1, ok), (2, ok), (3, bad), (-1, bad)):
+        assert so.mbl_set_gram_engine(eng) == want
+    so.mbl_set_gram_engine(0)
 
 
 def test_autotune_checks_arguments_before_any_launch(so):

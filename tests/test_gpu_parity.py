@@ -311,3 +311,25 @@ def test_autotune_keeps_a_correct_choice(mbl, L, periodic, k, dtype):
     ref = ham.apply(chain, 0.25, Xh.astype(np.float64))
     err = np.abs(Y.cpu().numpy().astype(np.float64) - ref)
     assert np.all(err <= _bound(chain, 0.25, Xh, dtype)), err.max()
+
+
+# ---------------------------------------------------------------- Gram (Rayleigh-Ritz)
+@pytest.mark.parametrize("n,p,q", [(1000, 8, 8), (4099, 32, 32), (20000, 96, 96), (184756, 96, 96),
+                                   (30001, 192, 192), (5000, 64, 160), (777, 256, 16)])
+@pytest.mark.parametrize("engine", [1, 2])
+def test_gram_engines_match_fp64(mbl, n, p, q, engine):
+    """C = A^T B in FP32 on the CUDA cores and on the tensor cores (tcgen05, TF32 split)
+    against numpy FP64: |C - C64| <= c * 2^-21 * (|A|^T |B|) elementwise."""
+    rng = np.random.default_rng(n + p + q)
+    A = rng.standard_normal((n, p))
+    B = rng.standard_normal((n, q)) * np.linspace(0.5, 3.0, q)
+    C = mbl.binding.gram(_gpu(A), _gpu(B), "f32", engine).cpu().numpy()
+    ref = A.T @ B
+    scale = np.abs(A).T @ np.abs(B)
+    err = np.abs(C - ref)
+    assert np.all(err <= 8 * 2.0 ** -21 * scale), (err / scale).max()
+    if engine == 2:
+        # the split recovers FP32 accuracy: single-pass TF32 would leave errors near 2^-11
+        assert (err / scale).max() < 2.0 ** -18
+    C64 = mbl.binding.gram(_gpu(A), _gpu(B), "f64", 1).cpu().numpy()
+    assert np.abs(C64 - ref).max() <= 1e-12 * scale.max()

@@ -210,3 +210,22 @@ def test_staged_schedule_solve_matches_dense(mbl, mode):
     assert stats["converged"] == 1
     assert np.abs(evals - want).max() <= (1e-9 if mode == 0 else 1e-6) * nh
     _certify(L, h, True, evals, vecs, nh)
+
+
+@pytest.mark.parametrize("L,k,nev", [(14, 32, 16), (16, 64, 24)])
+def test_tensor_core_grams_solve_matches_dense(mbl, L, k, nev):
+    """Mixed mode with its FP32 Grams on the tensor cores (tcgen05 kind::tf32, two-term
+    TF32 split): the eigenvalues nearest sigma still match dense LAPACK."""
+    h = wl.fields(L, 8.0, 2)
+    ev = np.linalg.eigvalsh(ham.dense_sector(ham.Chain(L, h, periodic=True)))
+    sigma = 0.5 * (ev[0] + ev[-1])
+    nh = max(abs(ev[0]), abs(ev[-1]))
+    want = np.sort(ev[np.lexsort((ev, np.abs(ev - sigma)))[:nev]])
+    try:
+        mbl.binding.set_gram_engine(2)
+        evals, resid, stats, vecs = _solve(mbl, L, h, True, sigma, nev, k, 1, nh, 40, 3)
+    finally:
+        mbl.binding.set_gram_engine(0)
+    assert stats["converged"] == 1
+    assert np.abs(evals - want).max() <= 1e-6 * nh
+    _certify(L, h, True, evals, vecs, nh)
