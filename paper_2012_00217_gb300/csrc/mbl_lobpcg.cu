@@ -206,11 +206,14 @@ struct Solver {
         return apply64(b.Tmp, k, Yp, ldy);
     }
     // X <- X - X_ref (X_ref^T X), twice (block classical Gram-Schmidt against X)
+    // B -= X (X^T B), twice.  B is a search direction (W from the preconditioner, or P):
+    // the Rayleigh-Ritz that follows resolves it only to FP32 in mixed mode, so the
+    // projection runs in FP32 there (X itself and every residual stay FP64).
     int ortho_against_x(double *Bp)
     {
         for (int pass = 0; pass < 2; ++pass) {
-            MBL_TRY(gram(X(), ld3(), k, Bp, ld3(), k, n, b.Gk, k, 0, 0, b.part, st));
-            MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, Bp, ld3(), Bp, ld3(), n, -1.0, 1.0, 0, st));
+            MBL_TRY(gram(X(), ld3(), k, Bp, ld3(), k, n, b.Gk, k, 0, gmix, b.part, st));
+            MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, Bp, ld3(), Bp, ld3(), n, -1.0, 1.0, gmix, st));
         }
         return MBL_OK;
     }
@@ -298,7 +301,9 @@ struct Solver {
         mark(5);
         // 7. updates
         MBL_TRY(update(b.S, ld3(), w, b.coef, k, k, nullptr, 0, b.Xn, k, n, 1.0, 0.0, 0, st));
-        MBL_TRY(update(W(), ld3(), w - k, b.coef + (int64_t)k * k, k, k, nullptr, 0, P(), ld3(), n, 1.0, 0.0, 0, st));
+        // the new direction P = [W P] C_WP: FP32 in mixed mode, like W and P themselves
+        MBL_TRY(update(W(), ld3(), w - k, b.coef + (int64_t)k * k, k, k, nullptr, 0, P(), ld3(), n, 1.0, 0.0, gmix,
+                       st));
         MBL_TRY(colnorms(P(), ld3(), k, n, b.rn, 1, b.part, st));
         MBL_TRY(scale_cols_inv(P(), ld3(), k, n, b.rn, st));
         MBL_TRY(cholqr_into_x(b.Xn, k));
