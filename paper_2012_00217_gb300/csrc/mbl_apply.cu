@@ -954,6 +954,20 @@ static int host_colex_rank(uint32_t u)
     return r;
 }
 
+int ensure_lowtab(int B);
+
+// Every tile width a product of this chain length may use, uploaded before a solve
+// captures its iteration into a CUDA graph (the upload is a synchronous copy, which a
+// capturing thread must not issue).
+int ensure_lowtabs_for(int L)
+{
+    for (int B = 2; B <= kLowMaxB && B <= L - 2; ++B) {
+        const int rc = ensure_lowtab(B);
+        if (rc != MBL_OK) return rc;
+    }
+    return MBL_OK;
+}
+
 int ensure_lowtab(int B)
 {
     if (B < 2 || B > kLowMaxB) return MBL_ERR_ARG;

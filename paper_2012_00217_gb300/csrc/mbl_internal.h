@@ -28,6 +28,8 @@ void note_launch(int64_t count = 1);
 void set_capturing(bool on);
 
 int num_sms();
+// Upload the low-pattern tables of every tile width usable at chain length L.
+int ensure_lowtabs_for(int L);
 int make_chain_params(const mbl_chain *chain, double sigma, ChainParams *cp);
 int apply_device(const ChainParams &cp, int dtype, const void *X, int64_t ldx, void *Y, int64_t ldy, uint32_t n,
                  int k, cudaStream_t st);

@@ -484,6 +484,7 @@ extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_
         s.mark(9);
     }
     // sector basis, read by every product kernel of the solve
+    MBL_TRY(ensure_lowtabs_for(chain->L));  // before any graph capture
     MBL_TRY(mbl_basis_build(chain->L, chain->n_up, s.b.states, n, stream));
     s.cp.states = s.b.states;
     // norm used to scale the tolerance
@@ -635,6 +636,7 @@ static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, c
     if (cudaMemsetAsync(s.b.counter, 0, 4 * sizeof(unsigned), st) != cudaSuccess ||
         cudaMemsetAsync(s.b.iflags, 0, (16 + 64) * sizeof(int), st) != cudaSuccess)
         return MBL_ERR_CUDA;
+    MBL_TRY(ensure_lowtabs_for(chain->L));  // before any graph capture
     MBL_TRY(mbl_basis_build(chain->L, chain->n_up, s.b.states, n, (mbl_stream_t)st));
     s.cp.states = s.b.states;
     MBL_TRY(s.cholqr_into_x(X0, ldx0));
@@ -644,6 +646,7 @@ static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, c
     bool have_p = false;
     int it = 0;
     double theta = 0.0, rn0 = 0.0;
+    GraphCache gc;  // the iteration body, captured once per shape and replayed
     for (;;) {
         if (cudaMemcpyAsync(&theta, s.b.Gk, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&rn0, s.b.rn, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -651,7 +654,7 @@ static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, c
             return MBL_ERR_CUDA;
         if (!std::isfinite(theta) || !std::isfinite(rn0)) return MBL_ERR_NUMERIC;
         if (rn0 <= tol * fabs(theta) || it >= max_iter) break;
-        MBL_TRY(s.enqueue_body(have_p));
+        MBL_TRY(run_body(s, have_p, true, gc));
         have_p = true;
         ++it;
     }

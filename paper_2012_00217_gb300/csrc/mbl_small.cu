@@ -190,6 +190,51 @@ __device__ int dev_chol_inv(int n, const double *G, int ldg, double *R, double *
     return bad;
 }
 
+// In-place upper Cholesky R^T R = A of the symmetric n x n matrix A (row stride ld, both
+// triangles on entry; the upper one holds R on exit) when every pivot exceeds tol (A has a
+// unit diagonal here, so tol bounds its conditioning); returns false (in every thread) as
+// soon as one does not.
+template <typename T>
+__device__ bool dev_chol_upper(int n, T *A, int ld, T tol, int *s_flag)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) *s_flag = 0;
+    __syncthreads();
+    for (int kk = 0; kk < n; ++kk) {
+        if (tid == 0) {
+            const T d = A[kk * ld + kk];
+            if (!(d > tol) || !isfinite(d)) *s_flag = 1;
+            else A[kk * ld + kk] = sqrt(d);
+        }
+        __syncthreads();
+        if (*s_flag) return false;
+        const T piv = A[kk * ld + kk];
+        for (int j = kk + 1 + tid; j < n; j += nt) A[kk * ld + j] /= piv;
+        __syncthreads();
+        const int m = n - kk - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = kk + 1 + e / m, j = kk + 1 + e % m;
+            if (j >= i) A[i * ld + j] -= A[kk * ld + i] * A[kk * ld + j];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// Ri = R^-1 for the upper-triangular R (row strides ldr, ldi), one column per thread.
+template <typename T>
+__device__ void dev_tri_inv_upper(int n, const T *R, int ldr, T *Ri, int ldi)
+{
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+        for (int i = n - 1; i >= 0; --i) {
+            T s = (i == j) ? (T)1 : (T)0;
+            if (i < j)
+                for (int m = i + 1; m <= j; ++m) s -= R[i * ldr + m] * Ri[m * ldi + j];
+            Ri[i * ldi + j] = (i <= j) ? s / R[i * ldr + i] : (T)0;
+        }
+    __syncthreads();
+}
+
 // C (rows x cols, stride ldc) = op(A) op(B) in precision TA, one output per thread step.
 // transA: A stored (inner x rows), else (rows x inner); B stored (inner x cols).
 template <typename TC, typename TA, typename TB>
@@ -263,9 +308,10 @@ int small_chol_inv(int n, const double *G, int64_t ldg, double *Rinv, double *wo
 }
 
 // ---------------------------------------------------------------------------------
-// SVQB + Rayleigh-Ritz on span(S), S = [X W P] with w columns (Stathopoulos & Wu):
-//   D = diag(G_S)^-1/2, eig(D G_S D) = U L U^T, keep L_i > tau max L,
-//   C_S = D U_keep L_keep^-1/2, eig(C_S^T G_A C_S) = Z theta,
+// Rayleigh-Ritz on span(S), S = [X W P] with w columns, in an S-orthonormal basis C_S:
+//   D = diag(G_S)^-1/2; Cholesky D G_S D = R^T R when every pivot is well above zero,
+//   C_S = D R^-1; else SVQB (Stathopoulos & Wu): eig(D G_S D) = U L U^T, keep
+//   L_i > tau max L, C_S = D U_keep L_keep^-1/2.  Then eig(C_S^T G_A C_S) = Z theta,
 //   coef = C_S Z[:, first k]  (the k smallest; the k largest, descending, if 'largest').
 // T is the precision of the two w x w eigensolves.  With T = float a k-dimensional FP64
 // refinement follows: Y = C_S Z_k R^-1 (R^T R = Z_k^T Z_k), M = Y^T G_A Y, eig(M) = Q mu
@@ -321,28 +367,50 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
         A[i * ld + j] = (T)(dsc[i] * 0.5 * (GS[i * w + j] + GS[j * w + i]) * dsc[j]);
     }
     __syncthreads();
-    dev_jacobi<T>(w, ld, A, V, csb, pairs, &s_rot, kMaxSweeps);
-    dev_sort_eig<T, T>(w, ld, A, V, lam, U, w);
-    if (tid == 0) {
-        const double lmax = (double)lam[w - 1];
-        int first = w;
-        for (int i = 0; i < w; ++i)
-            if ((double)lam[i] > tau * lmax) {
-                first = i;
-                break;
-            }
-        s_first = first;
-        s_keep = w - first;
+    // An S-orthonormal basis: from the Cholesky factor of D G_S D when that is well
+    // conditioned (every pivot of the unit-diagonal matrix above chol_tol), C_S = D R^-1,
+    // all w directions kept; otherwise SVQB, which drops the nearly dependent directions.
+    const T chol_tol = sizeof(T) == sizeof(float) ? (T)1e-3 : (T)1e-8;
+    for (int e = tid; e < w * w; e += nt) T2[e] = A[(e / w) * ld + (e % w)];
+    const bool chol = dev_chol_upper<T>(w, T2, w, chol_tol, &s_flag);
+    if (chol) {
+        dev_tri_inv_upper<T>(w, T2, w, U, w);
+        for (int e = tid; e < w * w; e += nt) {
+            const int i = e / w;
+            const double c = dsc[i] * (double)U[e];
+            Cs[e] = c;
+            Cst[e] = (T)c;
+        }
+        if (tid == 0) {
+            s_first = 0;
+            s_keep = w;
+        }
+        __syncthreads();
+    } else {
+        dev_jacobi<T>(w, ld, A, V, csb, pairs, &s_rot, kMaxSweeps);
+        dev_sort_eig<T, T>(w, ld, A, V, lam, U, w);
+        if (tid == 0) {
+            const double lmax = (double)lam[w - 1];
+            int first = w;
+            for (int i = 0; i < w; ++i)
+                if ((double)lam[i] > tau * lmax) {
+                    first = i;
+                    break;
+                }
+            s_first = first;
+            s_keep = w - first;
+        }
+        __syncthreads();
+        const int first = s_first, keep = s_keep;
+        for (int e = tid; e < w * keep; e += nt) {
+            const int i = e / keep, j = e - (e / keep) * keep;
+            const double c = dsc[i] * (double)U[i * w + first + j] / sqrt((double)lam[first + j]);
+            Cs[i * w + j] = c;
+            Cst[i * w + j] = (T)c;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    const int first = s_first, keep = s_keep;
-    for (int e = tid; e < w * keep; e += nt) {
-        const int i = e / keep, j = e - (e / keep) * keep;
-        const double c = dsc[i] * (double)U[i * w + first + j] / sqrt((double)lam[first + j]);
-        Cs[i * w + j] = c;
-        Cst[i * w + j] = (T)c;
-    }
-    __syncthreads();
+    const int keep = s_keep;
     // projected G_A in precision T: T2 = G_A Cs, A = Cs^T T2 (keep x keep, stride ldk)
     const int ldk = pad_ld(keep);
     dev_matmul<T, T, T>(w, keep, w, GAt, w, false, Cst, w, T2, w);
