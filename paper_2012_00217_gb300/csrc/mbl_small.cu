@@ -534,55 +534,73 @@ int small_svqb_rr(int w, int k, int largest, int mixed, const double *GS, const 
 // Residual of pair j: sqrt(v_j^T EtE v_j).  Selects the nev values of mu nearest 0
 // (ties: lower first), writes sel (ascending mu), res_sel, st[0] = converged,
 // st[1] = NaN/Inf seen, dst[0] = max relative residual of the selection.
-__global__ void k_hrr_select(int k, int nev, const double *mu, const double *V, const double *EtE, double tol_abs,
-                             double norm_h, double *res_all, int *sel, double *res_sel, int *st, double *dst)
+// res_all[j] = sqrt(v_j^T sym(EtE) v_j), one block per column j: thread a forms
+// (sym(EtE) v_j)_a, the block sums v_j[a] times it in a fixed shape (warp shuffles, then
+// the warps in order).
+__global__ void __launch_bounds__(64) k_hrr_resid(int k, const double *V, const double *EtE, double *res_all)
 {
-    const int tid = threadIdx.x;
-    for (int j = tid; j < k; j += blockDim.x) {
-        double s = 0.0;
-        for (int a = 0; a < k; ++a) {
-            double t = 0.0;
-            for (int b = 0; b < k; ++b) t += 0.5 * (EtE[a * k + b] + EtE[b * k + a]) * V[b * k + j];
-            s += V[a * k + j] * t;
+    __shared__ double s_w[2];
+    const int j = blockIdx.x, a = threadIdx.x;
+    double s = 0.0;
+    if (a < k) {
+        double t = 0.0;
+        for (int b = 0; b < k; ++b) t += 0.5 * (EtE[a * k + b] + EtE[b * k + a]) * V[b * k + j];
+        s = V[a * k + j] * t;
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((a & 31) == 0) s_w[a >> 5] = s;
+    __syncthreads();
+    if (a == 0) res_all[j] = sqrt(fmax(s_w[0] + s_w[1], 0.0));
+}
+
+// The nev Ritz values nearest 0 (|mu| ascending, ties: lower mu, then lower index), in
+// ascending index order: thread j ranks its own value against all k, and the chosen
+// ones are compacted by ballot.
+__global__ void __launch_bounds__(64) k_hrr_pick(int k, int nev, const double *mu, const double *res_all,
+                                                 double tol_abs, double norm_h, int *sel, double *res_sel, int *st,
+                                                 double *dst)
+{
+    __shared__ unsigned s_ball[2];
+    __shared__ int s_conv[2], s_bad[2];
+    __shared__ double s_mx[2];
+    const int j = threadIdx.x, lane = j & 31, w = j >> 5;
+    bool pick = false;
+    if (j < k) {
+        const double mj = mu[j], aj = fabs(mj);
+        int rank = 0;
+        for (int i = 0; i < k; ++i) {
+            const double mi = mu[i], ai = fabs(mi);
+            if (ai < aj || (ai == aj && (mi < mj || (mi == mj && i < j)))) ++rank;
         }
-        res_all[j] = sqrt(fmax(s, 0.0));
+        pick = rank < nev;
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, pick);
+    if (lane == 0) s_ball[w] = ball;
+    __syncthreads();
+    int conv = 1, bad = 0;
+    double mx = 0.0;
+    if (pick) {
+        const int pos = __popc(ball & ((1u << lane) - 1u)) + (w ? __popc(s_ball[0]) : 0);
+        const double r = res_all[j];
+        sel[pos] = j;
+        res_sel[pos] = r;
+        if (!isfinite(r) || !isfinite(mu[j])) bad = 1;
+        if (!(r <= tol_abs)) conv = 0;
+        mx = r / norm_h;
+    }
+    conv = __all_sync(0xffffffffu, conv);
+    bad = __any_sync(0xffffffffu, bad);
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) {
+        s_conv[w] = conv;
+        s_bad[w] = bad;
+        s_mx[w] = mx;
     }
     __syncthreads();
-    if (tid == 0) {
-        int chosen[64];
-        int nc = 0;
-        for (int t = 0; t < nev; ++t) {
-            int best = -1;
-            for (int j = 0; j < k; ++j) {
-                bool used = false;
-                for (int u = 0; u < nc; ++u)
-                    if (chosen[u] == j) used = true;
-                if (used) continue;
-                if (best < 0 || fabs(mu[j]) < fabs(mu[best]) || (fabs(mu[j]) == fabs(mu[best]) && mu[j] < mu[best]))
-                    best = j;
-            }
-            chosen[nc++] = best;
-        }
-        for (int a = 0; a < nc; ++a)
-            for (int b = a + 1; b < nc; ++b)
-                if (chosen[b] < chosen[a]) {
-                    const int t = chosen[a];
-                    chosen[a] = chosen[b];
-                    chosen[b] = t;
-                }
-        int conv = 1, bad = 0;
-        double mx = 0.0;
-        for (int a = 0; a < nc; ++a) {
-            const double r = res_all[chosen[a]];
-            sel[a] = chosen[a];
-            res_sel[a] = r;
-            if (!isfinite(r) || !isfinite(mu[chosen[a]])) bad = 1;
-            if (!(r <= tol_abs)) conv = 0;
-            mx = fmax(mx, r / norm_h);
-        }
-        st[0] = conv;
-        st[1] = bad;
-        dst[0] = mx;
+    if (j == 0) {
+        st[0] = s_conv[0] && s_conv[1];
+        st[1] = s_bad[0] || s_bad[1];
+        dst[0] = fmax(s_mx[0], s_mx[1]);
     }
 }
 
@@ -590,7 +608,9 @@ int hrr_select(int k, int nev, const double *mu, const double *V, const double *
                double *res_all, int *sel, double *res_sel, int *st, double *dst, cudaStream_t s)
 {
     note_launch();
-    k_hrr_select<<<1, 64, 0, s>>>(k, nev, mu, V, EtE, tol_abs, norm_h, res_all, sel, res_sel, st, dst);
+    k_hrr_resid<<<k, 64, 0, s>>>(k, V, EtE, res_all);
+    note_launch();
+    k_hrr_pick<<<1, 64, 0, s>>>(k, nev, mu, res_all, tol_abs, norm_h, sel, res_sel, st, dst);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
 
