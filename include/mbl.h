@@ -273,8 +273,11 @@ int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, const double *s
 /* Spectrum bounds E_min, E_max of the sector Hamiltonian (used to place sigma at the
  * middle of the spectrum and to scale tolerances): unpreconditioned LOBPCG on +H and
  * on -H, block width k (2 <= k <= 16), stopping when the lowest Ritz pair has
- * ||B x - theta x|| <= tol |theta|.  X0_dev: n x k FP64 start block (ld = k).
- * Workspace: mbl_bounds_workspace_size bytes. */
+ * ||B x - theta x|| <= tol |theta|.  X0_dev: n x k FP64 start block (ld = k), read by
+ * both runs.  The two runs proceed concurrently: E_max on a helper host thread and
+ * stream ordered after `stream`, E_min on `stream`; `stream` is ordered after both when
+ * the call returns (host-synchronous).  Workspace: mbl_bounds_workspace_size bytes (two
+ * halves, one per run).  *iters_host: the iterations of both runs. */
 int mbl_bounds_workspace_size(const mbl_chain *chain, int k, size_t *bytes);
 int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, int max_iter,
                         const double *X0_dev, void *workspace_dev, size_t workspace_bytes,

@@ -68,6 +68,9 @@ struct PcgScalars {
     double *rz, *rz0, *alpha, *beta;
     int *active;
     double tol2;  // pcg_tol^2 (0: never freeze)
+    // when set (tiled kernels), the q-launch also does w += alpha p for its rows
+    void *w = nullptr;
+    const void *p = nullptr;
 };
 
 struct Reduce {
@@ -187,7 +190,8 @@ __device__ __forceinline__ void gather_add2(T (&acc0)[V], T (&acc1)[V], const T 
 template <typename T, int V, int MODE>
 __device__ __forceinline__ void finish_row(const T (&acc)[V], int f, uint32_t r, T *__restrict__ Y, int64_t ldy,
                                            T *__restrict__ R, const T *__restrict__ dinv, int col, const T (&alpha)[V],
-                                           T (&part)[V])
+                                           T (&part)[V], T *__restrict__ Wf = nullptr,
+                                           const T *__restrict__ Pf = nullptr)
 {
     if (f < 0) return;
     if (MODE == 0 || MODE == 1) {
@@ -211,6 +215,13 @@ __device__ __forceinline__ void finish_row(const T (&acc)[V], int f, uint32_t r,
             part[v] += rr.v[v] * (di * rr.v[v]);
         }
         stv<T, V>(R + (int64_t)r * ldy + col, rr);
+        if (Wf) {  // the solution update of the same PCG step, row by row
+            Vec<T, V> wv = ldv<T, V>(Wf + (int64_t)r * ldy + col);
+            const Vec<T, V> pv = ldv<T, V>(Pf + (int64_t)r * ldy + col);
+#pragma unroll
+            for (int v = 0; v < V; ++v) wv.v[v] += alpha[v] * pv.v[v];
+            stv<T, V>(Wf + (int64_t)r * ldy + col, wv);
+        }
     }
 }
 
@@ -602,7 +613,8 @@ __device__ __forceinline__ void tile_row_pass(const ChainParams &cp, int B, cons
                                               uint32_t j, bool valid, const TileMeta<T> &tm, const T *tab, T hdelta,
                                               uint32_t t0, uint32_t thi, uint32_t sup, uint32_t sdn, int col,
                                               T *__restrict__ Y, int64_t ldy, T *__restrict__ R,
-                                              const T *__restrict__ dinv, const T *s_alpha, T (&part)[V])
+                                              const T *__restrict__ dinv, const T *s_alpha, T (&part)[V],
+                                              void *ps_w, const void *ps_p)
 {
     const uint32_t r = tm.off + j;
     const T *__restrict__ xr = X + (int64_t)r * ldx + col;
@@ -691,7 +703,7 @@ __device__ __forceinline__ void tile_row_pass(const ChainParams &cp, int B, cons
         T alpha[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) alpha[v] = (MODE == kPcgQ) ? s_alpha[col + v] : (T)0;
-        finish_row<T, V, MODE>(acc, 0, r, Y, ldy, R, dinv, col, alpha, part);
+        finish_row<T, V, MODE>(acc, 0, r, Y, ldy, R, dinv, col, alpha, part, (T *)ps_w, (const T *)ps_p);
     }
 }
 
@@ -779,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(
         for (uint32_t j0 = j_begin; j0 < j_end; j0 += RPW) {
             const uint32_t j = j0 + grp;
             tile_row_pass<T, V, NB, MODE>(cp, B, X, ldx, Xt, ldx, rp, j, j < j_end, tm, tab, hdelta, t0, thi, sup,
-                                          sdn, col, Y, ldy, R, dinv, s_alpha, part);
+                                          sdn, col, Y, ldy, R, dinv, s_alpha, part, ps.w, ps.p);
         }
     }
     if (MODE == kPlain) return;
@@ -926,7 +938,7 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS)
         for (uint32_t j0 = warp * RPW; j0 < Rt; j0 += RPB) {
             const uint32_t j = j0 + grp;
             tile_row_pass<T, V, NB, MODE>(cp, B, X, K, s_tile, K, rp, j, j < Rt, s_meta, tab, hdelta, t0, thi, sup,
-                                          sdn, col, Y, K, R, dinv, s_alpha, part);
+                                          sdn, col, Y, K, R, dinv, s_alpha, part, ps.w, ps.p);
         }
         // every read of this tile is done before the next copy overwrites it
         __syncthreads();
@@ -1160,7 +1172,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(const double *__restrict_
 }
 
 // PCG direction update: w += alpha p_old; p = dinv r + beta p_old (per column scalars).
-template <typename T, int K>
+template <typename T, int K, bool WDONE>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(uint32_t n, const T *__restrict__ dinv,
                                                          const T *__restrict__ r, T *__restrict__ p,
                                                          T *__restrict__ w, PcgScalars ps)
@@ -1178,14 +1190,16 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(uint32_t n, const T *__
     for (uint32_t row = blockIdx.x * rows_per_block + threadIdx.x / G; row < n;
          row += gridDim.x * rows_per_block) {
         const int64_t o = (int64_t)row * K + col;
-        Vec<T, V> rv = ldv<T, V>(r + o), pv = ldv<T, V>(p + o), wv = ldv<T, V>(w + o);
+        Vec<T, V> rv = ldv<T, V>(r + o), pv = ldv<T, V>(p + o);
         const T di = dinv[row];
+        if (!WDONE) {  // else the q-launch has done w += alpha p
+            Vec<T, V> wv = ldv<T, V>(w + o);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            wv.v[v] += a[v] * pv.v[v];
-            pv.v[v] = di * rv.v[v] + bt[v] * pv.v[v];
+            for (int v = 0; v < V; ++v) wv.v[v] += a[v] * pv.v[v];
+            stv<T, V>(w + o, wv);
         }
-        stv<T, V>(w + o, wv);
+#pragma unroll
+        for (int v = 0; v < V; ++v) pv.v[v] = di * rv.v[v] + bt[v] * pv.v[v];
         stv<T, V>(p + o, pv);
     }
 }
@@ -1688,10 +1702,15 @@ static cudaError_t pcg_step_k(const ChainParams &cp, uint32_t n, const T *dinv, 
 {
     cudaError_t e;
     const int B = tile_bits_for(cp.L, K, sizeof(T));
+    bool wdone = false;
     if (B >= 2) {
         e = launch_tiled<T, K, kPcgT>(cp, B, p, K, t, K, nullptr, dinv, ps, rd, st);
         if (e != cudaSuccess) return e;
-        e = launch_tiled<T, K, kPcgQ>(cp, B, t, K, nullptr, K, r, dinv, ps, rd, st);
+        PcgScalars psq = ps;  // the q-launch also updates w (alpha is known by then)
+        psq.w = w;
+        psq.p = p;
+        e = launch_tiled<T, K, kPcgQ>(cp, B, t, K, nullptr, K, r, dinv, psq, rd, st);
+        wdone = true;
     } else {
         e = launch_apply_k<T, K, kPcgT>(cp, p, K, t, K, n, nullptr, dinv, ps, rd, grid, st);
         if (e != cudaSuccess) return e;
@@ -1701,7 +1720,8 @@ static cudaError_t pcg_step_k(const ChainParams &cp, uint32_t n, const T *dinv, 
     int ugrid = (int)(((int64_t)n * RowLayout<T, K>::G + kThreads - 1) / kThreads);
     note_launch();
     if (ugrid > num_sms() * 8) ugrid = num_sms() * 8;
-    k_pcg_update<T, K><<<ugrid, kThreads, 0, st>>>(n, dinv, r, p, w, ps);
+    if (wdone) k_pcg_update<T, K, true><<<ugrid, kThreads, 0, st>>>(n, dinv, r, p, w, ps);
+    else k_pcg_update<T, K, false><<<ugrid, kThreads, 0, st>>>(n, dinv, r, p, w, ps);
     return cudaGetLastError();
 }
 

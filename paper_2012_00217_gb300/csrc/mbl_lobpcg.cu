@@ -610,7 +610,9 @@ extern "C" int mbl_bounds_workspace_size(const mbl_chain *chain, int k, size_t *
     if (!chain || !bytes || k < 2 || k > 16) return MBL_ERR_ARG;
     int64_t n = mbl_basis_size(chain->L, chain->n_up);
     if (n <= 0 || (int64_t)3 * k > n) return MBL_ERR_ARG;
-    carve(nullptr, n, k, 1, bytes);
+    size_t slot = 0;
+    carve(nullptr, n, k, 1, &slot);
+    *bytes = 2 * ((slot + 255) & ~(size_t)255);  // one slot per end of the spectrum
     return MBL_OK;
 }
 
@@ -676,12 +678,44 @@ extern "C" int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, in
     rc = make_chain_params(chain, 0.0, &cp);
     if (rc != MBL_OK) return rc;
     if (iters_host) *iters_host = 0;
+    // The two ends are independent LOBPCG runs, each host-synchronous per iteration: E_max
+    // runs on a helper thread and stream (ordered after the caller's stream) while E_min
+    // runs here, each in its own half of the workspace.
+    const size_t slot = need / 2;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MBL_ERR_CUDA;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) return MBL_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev_start, (cudaStream_t)stream) != cudaSuccess || cudaStreamWaitEvent(s2, ev_start, 0) != cudaSuccess) {
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_done) cudaEventDestroy(ev_done);
+        cudaStreamDestroy(s2);
+        return MBL_ERR_CUDA;
+    }
     double lo = 0.0, hi = 0.0;
-    int r1 = bounds_one(chain, k, tol, max_iter, X0_dev, k, workspace_dev, workspace_bytes, 0, &lo, iters_host,
+    int it_lo = 0, it_hi = 0, r2 = MBL_OK;
+    std::thread helper([&]() {
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            r2 = MBL_ERR_CUDA;
+            return;
+        }
+        r2 = bounds_one(chain, k, tol, max_iter, X0_dev, k, (char *)workspace_dev + slot, slot, 1, &hi, &it_hi, s2);
+    });
+    int r1 = bounds_one(chain, k, tol, max_iter, X0_dev, k, workspace_dev, slot, 0, &lo, &it_lo,
                         (cudaStream_t)stream);
+    helper.join();
+    // later work on the caller's stream comes after the helper stream's last kernel
+    const bool joined = cudaEventRecord(ev_done, s2) == cudaSuccess &&
+                        cudaStreamWaitEvent((cudaStream_t)stream, ev_done, 0) == cudaSuccess;
+    cudaEventDestroy(ev_start);
+    cudaEventDestroy(ev_done);
+    cudaStreamDestroy(s2);
+    if (!joined) return MBL_ERR_CUDA;
+    if (iters_host) *iters_host = it_lo + it_hi;
     if (r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) return r1;
-    int r2 = bounds_one(chain, k, tol, max_iter, X0_dev, k, workspace_dev, workspace_bytes, 1, &hi, iters_host,
-                        (cudaStream_t)stream);
     if (r2 != MBL_OK && r2 != MBL_ERR_NOT_CONVERGED) return r2;
     if (emin_host) *emin_host = lo;
     if (emax_host) *emax_host = hi;
