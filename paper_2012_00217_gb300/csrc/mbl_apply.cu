@@ -40,16 +40,23 @@ struct RowLayout {
 };
 
 // Tiled kernels move up to LB bytes per lane (LB = 16 or 32) of every neighbour row.
+#ifndef MBL_CH_PASSES
+#define MBL_CH_PASSES 4
+#endif
+#ifndef MBL_CH_MIN
+#define MBL_CH_MIN 32
+#endif
+
 template <typename T, int K, int LB = 32>
 struct WideRowLayout {
     static constexpr int kBytes = K * (int)sizeof(T);
     static constexpr int V = kBytes >= LB ? LB / (int)sizeof(T) : K;
     static constexpr int G = K / V;
     static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "unsupported row width");
-    // rows per work item of the tiled product: at least four row-passes of the warp
-    // (32 / G rows each) and at least 32 rows, so the per-tile setup of an item (tile
-    // offset, high-bond shifts) is spread over enough rows
-    static constexpr int CH = (4 * (32 / G) > 32) ? 4 * (32 / G) : 32;
+    // rows per work item of the tiled product: at least MBL_CH_PASSES row-passes of the
+    // warp (32 / G rows each) and at least MBL_CH_MIN rows, so the per-tile setup of an
+    // item (tile offset, high-bond shifts) is spread over enough rows
+    static constexpr int CH = (MBL_CH_PASSES * (32 / G) > MBL_CH_MIN) ? MBL_CH_PASSES * (32 / G) : MBL_CH_MIN;
 };
 
 constexpr int kThreads = 256;
