@@ -318,7 +318,7 @@ def solve_kernel_roofline(torch, mbl, dev, s, peak_gbs):
     t_warm = _graph_time(torch, fn, 50)
     t_cold = _graph_time(torch, fn, 20, flush)
     alg = 2.0 * n * k * 4
-    return dict(kernel="k_apply_tiled<float,32> (PCG block product)", alg_bytes=alg, t_l2_warm_us=t_warm * 1e6,
+    return dict(kernel="tiled product <float,32> (the PCG block product)", alg_bytes=alg, t_l2_warm_us=t_warm * 1e6,
                 t_cold_us=t_cold * 1e6, gbs_cold=alg / t_cold / 1e9, gbs_warm=alg / t_warm / 1e9)
 
 
@@ -600,7 +600,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": kern["gbs_warm"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": kern["gbs_warm"] / peaks["hbm_gbs"],
                      "traffic": profiled_traffic("L20_k32_f32"),
-                     "kernel": kern["kernel"] + ", algorithmic 2nk*4 B per launch / CUDA-event launch time",
+                     "kernel": kern["kernel"] + " under the autotuned schedule %d (1 persistent, 2 ordered, 3 "
+                               "staged), algorithmic 2nk*4 B per launch / CUDA-event launch time" % tuned["f32"]["schedule"],
                      "peak_kind": peak_kind + " (hbm_gbs)"},
         "matvec_roofline": None,
         "solve_kernel": kern,
@@ -616,7 +617,8 @@ def main():
         line["matvec_roofline"] = {"bound": "hbm", "achieved": head["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                    "frac": head["gbs"] / peaks["hbm_gbs"],
                                    "traffic": profiled_traffic("L26_k64_f32"),
-                                   "kernel": "k_apply_tiled<float,64> L=26 open k=64 (block product), L2 flushed",
+                                   "kernel": "tiled product <float,64> L=26 open k=64, schedule %d, L2 flushed"
+                                             % head["tuned"]["schedule"],
                                    "peak_kind": peak_kind + " (hbm_gbs)"}
     if rank == 0 and world == 1 and not args.quick:
         line["cpu_baseline"] = cpu_baseline(s, res["stats"]["iters"])
