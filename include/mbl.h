@@ -271,13 +271,15 @@ int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, const double *s
                              mbl_stream_t stream);
 
 /* Spectrum bounds E_min, E_max of the sector Hamiltonian (used to place sigma at the
- * middle of the spectrum and to scale tolerances): unpreconditioned LOBPCG on +H and
- * on -H, block width k (2 <= k <= 16), stopping when the lowest Ritz pair has
- * ||B x - theta x|| <= tol |theta|.  X0_dev: n x k FP64 start block (ld = k), read by
- * both runs.  The two runs proceed concurrently: E_max on a helper host thread and
- * stream ordered after `stream`, E_min on `stream`; `stream` is ordered after both when
- * the call returns (host-synchronous).  Workspace: mbl_bounds_workspace_size bytes (two
- * halves, one per run).  *iters_host: the iterations of both runs. */
+ * middle of the spectrum and to scale tolerances): one FP64 Lanczos recurrence on H
+ * started from column 0 of X0_dev (n x k FP64, ld = k; the other columns are not read;
+ * 2 <= k <= 16 and 3k <= n are checked), without reorthogonalisation.  Every 20 steps the
+ * extreme eigenvalues theta of the tridiagonal T_m are found by Sturm bisection and each
+ * end's residual ||H y - theta y|| = beta_m |last component of T_m's eigenvector| by
+ * inverse iteration; the call stops when both are <= tol |theta| (or the recurrence
+ * meets an invariant subspace), or after max_iter steps (at most 4096; then
+ * MBL_ERR_NOT_CONVERGED with the current estimates).  *iters_host: the Lanczos steps.
+ * Host-synchronous every 20 steps.  Workspace: mbl_bounds_workspace_size bytes. */
 int mbl_bounds_workspace_size(const mbl_chain *chain, int k, size_t *bytes);
 int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, int max_iter,
                         const double *X0_dev, void *workspace_dev, size_t workspace_bytes,

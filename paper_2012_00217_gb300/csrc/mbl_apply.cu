@@ -864,8 +864,12 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+#ifndef MBL_STAGED_MIN_BLOCKS
+#define MBL_STAGED_MIN_BLOCKS 3
+#endif
+
 template <typename T, int K, int MODE, int LB>
-__global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, MBL_STAGED_MIN_BLOCKS)
     k_apply_staged(ChainParams cp, int B, const T *__restrict__ X, T *__restrict__ Y, T *__restrict__ R,
                    const T *__restrict__ dinv, PcgScalars ps, Reduce rd)
 {

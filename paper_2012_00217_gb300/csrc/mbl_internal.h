@@ -28,6 +28,10 @@ void note_launch(int64_t count = 1);
 void set_capturing(bool on);
 
 int num_sms();
+// Spectrum bounds by FP64 Lanczos on H (mbl_lanczos.cu); X0: start vector in column 0 (ld).
+size_t lanczos_workspace_bytes(int64_t n);
+int lanczos_bounds(const ChainParams &cp, int64_t n, const double *X0, int64_t ldx0, double tol, int max_iter,
+                   void *ws, size_t ws_bytes, double *emin, double *emax, int *iters, cudaStream_t st);
 // Upload the low-pattern tables of every tile width usable at chain length L.
 int ensure_lowtabs_for(int L);
 int make_chain_params(const mbl_chain *chain, double sigma, ChainParams *cp);

@@ -610,59 +610,8 @@ extern "C" int mbl_bounds_workspace_size(const mbl_chain *chain, int k, size_t *
     if (!chain || !bytes || k < 2 || k > 16) return MBL_ERR_ARG;
     int64_t n = mbl_basis_size(chain->L, chain->n_up);
     if (n <= 0 || (int64_t)3 * k > n) return MBL_ERR_ARG;
-    size_t slot = 0;
-    carve(nullptr, n, k, 1, &slot);
-    *bytes = 2 * ((slot + 255) & ~(size_t)255);  // one slot per end of the spectrum
+    *bytes = lanczos_workspace_bytes(n);
     return MBL_OK;
-}
-
-static int bounds_one(const mbl_chain *chain, int k, double tol, int max_iter, const double *X0, int64_t ldx0,
-                      void *ws, size_t ws_bytes, int largest, double *theta_out, int *iters, cudaStream_t st)
-{
-    int64_t n = mbl_basis_size(chain->L, chain->n_up);
-    Solver s;
-    MBL_TRY(make_chain_params(chain, 0.0, &s.cp));
-    size_t need = 0;
-    s.b = carve((char *)ws, n, k, 1, &need);
-    if (ws_bytes < need) return MBL_ERR_WORKSPACE;
-    s.n = n;
-    s.k = k;
-    s.nev = 1;
-    s.m = 0;
-    s.mixed = 0;
-    s.gmix = 0;
-    s.largest = largest;
-    s.folded = 0;
-    s.pcg_tol = 0.0;
-    s.st = st;
-    if (cudaMemsetAsync(s.b.counter, 0, 4 * sizeof(unsigned), st) != cudaSuccess ||
-        cudaMemsetAsync(s.b.iflags, 0, (16 + 64) * sizeof(int), st) != cudaSuccess)
-        return MBL_ERR_CUDA;
-    MBL_TRY(ensure_lowtabs_for(chain->L));  // before any graph capture
-    MBL_TRY(mbl_basis_build(chain->L, chain->n_up, s.b.states, n, (mbl_stream_t)st));
-    s.cp.states = s.b.states;
-    MBL_TRY(s.cholqr_into_x(X0, ldx0));
-    MBL_TRY(s.refresh_tx());
-    MBL_TRY(initial_rr(s));
-    MBL_TRY(s.enqueue_bounds_status());
-    bool have_p = false;
-    int it = 0;
-    double theta = 0.0, rn0 = 0.0;
-    GraphCache gc;  // the iteration body, captured once per shape and replayed
-    for (;;) {
-        if (cudaMemcpyAsync(&theta, s.b.Gk, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(&rn0, s.b.rn, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return MBL_ERR_CUDA;
-        if (!std::isfinite(theta) || !std::isfinite(rn0)) return MBL_ERR_NUMERIC;
-        if (rn0 <= tol * fabs(theta) || it >= max_iter) break;
-        MBL_TRY(run_body(s, have_p, true, gc));
-        have_p = true;
-        ++it;
-    }
-    *theta_out = theta;
-    if (iters) *iters += it;
-    return (rn0 <= tol * fabs(theta)) ? MBL_OK : MBL_ERR_NOT_CONVERGED;
 }
 
 extern "C" int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, int max_iter, const double *X0_dev,
@@ -672,54 +621,21 @@ extern "C" int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, in
     size_t need = 0;
     int rc = mbl_bounds_workspace_size(chain, k, &need);
     if (rc != MBL_OK) return rc;
-    if (!X0_dev || !workspace_dev || !(tol > 0.0) || max_iter < 0) return MBL_ERR_ARG;
+    if (!X0_dev || !workspace_dev || !(tol > 0.0) || max_iter < 1) return MBL_ERR_ARG;
     if (workspace_bytes < need) return MBL_ERR_WORKSPACE;
     ChainParams cp;
     rc = make_chain_params(chain, 0.0, &cp);
     if (rc != MBL_OK) return rc;
+    MBL_TRY(ensure_lowtabs_for(chain->L));
     if (iters_host) *iters_host = 0;
-    // The two ends are independent LOBPCG runs, each host-synchronous per iteration: E_max
-    // runs on a helper thread and stream (ordered after the caller's stream) while E_min
-    // runs here, each in its own half of the workspace.
-    const size_t slot = need / 2;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return MBL_ERR_CUDA;
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
-    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) return MBL_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventRecord(ev_start, (cudaStream_t)stream) != cudaSuccess || cudaStreamWaitEvent(s2, ev_start, 0) != cudaSuccess) {
-        if (ev_start) cudaEventDestroy(ev_start);
-        if (ev_done) cudaEventDestroy(ev_done);
-        cudaStreamDestroy(s2);
-        return MBL_ERR_CUDA;
-    }
     double lo = 0.0, hi = 0.0;
-    int it_lo = 0, it_hi = 0, r2 = MBL_OK;
-    std::thread helper([&]() {
-        if (cudaSetDevice(dev) != cudaSuccess) {
-            r2 = MBL_ERR_CUDA;
-            return;
-        }
-        r2 = bounds_one(chain, k, tol, max_iter, X0_dev, k, (char *)workspace_dev + slot, slot, 1, &hi, &it_hi, s2);
-    });
-    int r1 = bounds_one(chain, k, tol, max_iter, X0_dev, k, workspace_dev, slot, 0, &lo, &it_lo,
+    const int64_t n = mbl_basis_size(chain->L, chain->n_up);
+    rc = lanczos_bounds(cp, n, X0_dev, k, tol, max_iter, workspace_dev, workspace_bytes, &lo, &hi, iters_host,
                         (cudaStream_t)stream);
-    helper.join();
-    // later work on the caller's stream comes after the helper stream's last kernel
-    const bool joined = cudaEventRecord(ev_done, s2) == cudaSuccess &&
-                        cudaStreamWaitEvent((cudaStream_t)stream, ev_done, 0) == cudaSuccess;
-    cudaEventDestroy(ev_start);
-    cudaEventDestroy(ev_done);
-    cudaStreamDestroy(s2);
-    if (!joined) return MBL_ERR_CUDA;
-    if (iters_host) *iters_host = it_lo + it_hi;
-    if (r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) return r1;
-    if (r2 != MBL_OK && r2 != MBL_ERR_NOT_CONVERGED) return r2;
+    if (rc != MBL_OK && rc != MBL_ERR_NOT_CONVERGED) return rc;
     if (emin_host) *emin_host = lo;
     if (emax_host) *emax_host = hi;
-    return (r1 == MBL_OK && r2 == MBL_OK) ? MBL_OK : MBL_ERR_NOT_CONVERGED;
+    return rc;
 }
 
 // ------------------------------------------------------------------------------------
@@ -873,13 +789,14 @@ extern "C" int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, cons
                 double lo = 0.0, hi = 0.0;
                 int it = 0;
                 const double *xb = X0_dev + off_x[i];
-                int r1 = bounds_one(&ch, kBatchBoundsK, kBatchBoundsTol, 1000, xb, opts->k, ws, slot, 0, &lo, &it, st);
-                int r2 = (r1 == MBL_OK || r1 == MBL_ERR_NOT_CONVERGED)
-                             ? bounds_one(&ch, kBatchBoundsK, kBatchBoundsTol, 1000, xb, opts->k, ws, slot, 1, &hi,
-                                          &it, st)
-                             : r1;
-                if ((r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) || (r2 != MBL_OK && r2 != MBL_ERR_NOT_CONVERGED)) {
-                    first_error.store(r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED ? r1 : r2);
+                ChainParams cpb;
+                int r1 = make_chain_params(&ch, 0.0, &cpb);
+                if (r1 == MBL_OK) r1 = ensure_lowtabs_for(ch.L);
+                if (r1 == MBL_OK)
+                    r1 = lanczos_bounds(cpb, mbl_basis_size(ch.L, ch.n_up), xb, opts->k, kBatchBoundsTol, 1000, ws,
+                                        slot, &lo, &hi, &it, st);
+                if (r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) {
+                    first_error.store(r1);
                     break;
                 }
                 sigma = 0.5 * (lo + hi);
