@@ -120,27 +120,41 @@ int mbl_set_product_tile_bits(int k, int dtype, int bits);
 int mbl_set_product_lane_bytes(int k, int dtype, int bytes);
 
 /* Tuning: work order of the tiled product for block width k and type dtype.
- * 0 = by size (default: ordered for plain products with rows of k * element size >= 256
- * bytes once C(L, n_up) * k * element size reaches 1 GiB in FP32 or 128 MiB in FP64,
- * else persistent), 1 = persistent (a few blocks per SM striding over the tiles),
- * 2 = ordered (plain products only: one chunk of rows per warp; the hardware dispatches
- * blocks in index order, so the tiles being read advance as a narrow window that stays
- * in L2), 3 = staged (each block copies whole tiles of at most 48 KB into shared memory
- * with bulk asynchronous copies and reads the in-tile neighbours there; needs rows of a
- * multiple of 16 bytes, ld = k and 16-byte aligned buffers, else persistent).  Results
- * are bitwise identical under orders 0-2 for the same tile width.  Returns MBL_ERR_ARG for
- * schedule outside 0..3, k outside 1..256 or an unknown dtype. */
+ * 0 = by size (default, unless mbl_autotune_product chose for this L: ordered for plain
+ * products with rows of k * element size >= 256 bytes once C(L, n_up) * k * element size
+ * reaches 1 GiB in FP32 or 128 MiB in FP64, staged for 128-byte rows from 16 MB, else
+ * persistent), 1 = persistent (a few blocks per SM striding over the tiles), 2 = ordered
+ * (plain products only: one chunk of rows per warp; the hardware dispatches blocks in
+ * index order, so the tiles being read advance as a narrow window that stays in L2),
+ * 3 = staged (each block copies whole tiles of at most 48 KB into shared memory with bulk
+ * asynchronous copies and reads the in-tile neighbours there), 4 = streamed (one block per
+ * SM; a producer warp copies every row block a tile's product reads -- joining-bond
+ * partners, wrap partner tile, the tile, one block per antiparallel high bond, and for the
+ * PCG launches the rows of r, w, p -- into a ring of shared-memory slots with bulk
+ * asynchronous copies, and the other warps add them up; rows of 32 to 512 bytes).  3 and
+ * 4 need ld = k and 16-byte aligned buffers (else persistent).  Results are bitwise
+ * identical under every order for the same tile width (mbl_product_tile_width).  Returns
+ * MBL_ERR_ARG for schedule outside 0..4, k outside 1..256 or an unknown dtype. */
 int mbl_set_product_schedule(int k, int dtype, int schedule);
+
+/* Tile width B (>= 2) that work order `schedule` (1..4, as above) uses for a chain of
+ * length L, block width k and type dtype under the current switches, or 0 when that
+ * order has no tiled kernel for this shape (3 and 4 then fall back to persistent, 1 and
+ * 2 to the untiled kernel).  Schedule 4 reads the device's shared-memory limit (a CUDA
+ * device must be current); 1..3 are host-only.  Returns MBL_ERR_ARG for an unknown dtype,
+ * k outside 1..256, L outside 4..32 or schedule outside 1..4. */
+int mbl_product_tile_width(int L, int dtype, int k, int schedule);
 
 /* Autotuner of the product (the tile widths and work orders above): times the plain
  * product of this chain, block width k, type dtype, under every candidate -- schedule
- * persistent / ordered / staged (where its conditions hold) times 32- or 64-byte lanes
- * (64 only for rows of >= 64 bytes) -- on the caller's buffers X_dev, Y_dev (n x k,
+ * persistent / ordered / staged / streamed (where its conditions hold) times 32- or
+ * 64-byte lanes (64 only for rows of >= 64 bytes; streamed has one lane width) -- on the
+ * caller's buffers X_dev, Y_dev (n x k,
  * ld = k, n = C(L, n_up); X is read, Y overwritten; they must not overlap): one warm-up
  * and `reps` timed launches each (1 <= reps <= 1000), CUDA events on `stream`.  The
  * fastest is kept for all later products with this L, k and dtype in this process (the
  * explicit switches above still take precedence) and reported in *choice (optional):
- * schedule 1..3, lane bytes, tile bits and the mean microseconds per product.  Widths k
+ * schedule 1..4, lane bytes, tile bits and the mean microseconds per product.  Widths k
  * without a tiled kernel leave nothing to choose: MBL_OK with *choice zeroed.
  * Host-synchronous (waits for its timing launches). */
 typedef struct {

@@ -34,7 +34,7 @@ EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis
             "mbl_set_product_tile_bits", "mbl_set_product_lane_bytes", "mbl_batched_workspace_size",
             "mbl_lobpcg_solve_batched", "mbl_kernel_launch_count",
             "mbl_set_product_schedule", "mbl_autotune_product", "mbl_set_gram_engine",
-            "mbl_gram_workspace_size", "mbl_gram")
+            "mbl_gram_workspace_size", "mbl_gram", "mbl_product_tile_width")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -102,6 +102,8 @@ def lib():
     so.mbl_set_product_lane_bytes.argtypes = [i32, i32, i32]
     so.mbl_set_product_schedule.restype = i32
     so.mbl_set_product_schedule.argtypes = [i32, i32, i32]
+    so.mbl_product_tile_width.restype = i32
+    so.mbl_product_tile_width.argtypes = [i32, i32, i32, i32]
     so.mbl_set_gram_engine.restype = i32
     so.mbl_set_gram_engine.argtypes = [i32]
     so.mbl_gram_workspace_size.restype = i32
@@ -228,10 +230,19 @@ def set_product_lane_bytes(k, dtype, nbytes):
 
 
 def set_product_schedule(k, dtype, schedule):
-    """mbl_set_product_schedule: 0 by size, 1 persistent, 2 ordered."""
+    """mbl_set_product_schedule: 0 by size, 1 persistent, 2 ordered, 3 staged, 4 streamed."""
     torch = _torch()
     dt = MBL_F32 if dtype == torch.float32 else MBL_F64
     _check(lib().mbl_set_product_schedule(int(k), dt, int(schedule)), "mbl_set_product_schedule")
+
+
+def product_tile_width(L, dtype, k, schedule):
+    """mbl_product_tile_width: the tile width B work order `schedule` uses (0: none)."""
+    torch = _torch()
+    dt = MBL_F32 if dtype == torch.float32 else MBL_F64
+    w = lib().mbl_product_tile_width(int(L), dt, int(k), int(schedule))
+    _check(w if w < 0 else MBL_OK, "mbl_product_tile_width")
+    return w
 
 
 def set_gram_engine(engine):

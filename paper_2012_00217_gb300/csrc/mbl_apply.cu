@@ -959,6 +959,387 @@ __global__ void __launch_bounds__(kThreads, MBL_STAGED_MIN_BLOCKS)
     pcg_block_finish<T, V, G, MODE>(red, part, K, ps, rd);
 }
 
+// ---------------------------------------------------------------------------------
+// Streamed tiled product: a few blocks per SM take whole tiles, and every row block the
+// product of a tile reads reaches shared memory by a bulk asynchronous copy.  Each term
+// of a tile's rows is one contiguous block of X: the joining-bond partners (the tile's
+// rows whose boundary spins differ, moved by one rank shift), the wrap partner tile, the
+// tile itself (own rows and in-tile neighbours), and one block per antiparallel high
+// bond (the tile's rows moved by that bond's rank shift).  The last warp of the block
+// is the producer: it walks the block's tiles and issues the copies, in that order, into
+// a ring of tile-sized slots (one full and one empty mbarrier per slot), so up to a ring
+// of data is in flight per SM without holding registers.  The other warps consume the
+// slots in the same order, adding each block into per-row accumulators: the sums are
+// formed in the order of the other work orders (joining, wrap, low bonds, high bonds)
+// and the result is bitwise that of k_apply_tiled at the same tile width.  PCG launches
+// also stream the rows of r (and w, p) their epilogue reads.  Rows of 32 to 512 bytes
+// (one 32-byte vector per lane), ld = K, 16-byte aligned bases.  Every mbarrier wait is
+// bounded; on a timeout the block stops copying, waits for the copies it issued, and
+// writes NaN to the rest of its output rows (and its PCG partials).
+
+constexpr int kMaxSlots = 12;
+#ifndef MBL_STREAM_PASSES
+#define MBL_STREAM_PASSES 3  // row groups of a consumer lane per tile
+#endif
+#ifndef MBL_STREAM_BLOCKS
+#define MBL_STREAM_BLOCKS 2  // resident blocks per SM (each with its own ring)
+#endif
+constexpr int kStreamPasses = MBL_STREAM_PASSES;
+constexpr int kStreamBlocks = MBL_STREAM_BLOCKS;
+
+#ifndef MBL_STREAM_MIN_SLOTS
+#define MBL_STREAM_MIN_SLOTS 6
+#endif
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// Bounded wait that also gives up once another warp of the block has flagged a failure.
+__device__ __forceinline__ bool ring_wait(uint64_t *mbar, unsigned parity, volatile int *fail)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity)) {
+        if (*fail) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *fail = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+template <typename T, int K>
+struct StreamLayout {
+    static constexpr int RB = K * (int)sizeof(T);  // row bytes
+    static constexpr int V = 32 / (int)sizeof(T);  // one 32-byte vector per lane
+    static constexpr int G = RB / 32;              // lanes per row
+    static constexpr int RPW = 32 / G;             // rows per warp and pass
+    static constexpr int NCW = kWarps - 1;         // consumer warps
+    static constexpr int RPP = NCW * RPW;          // rows per pass of the block
+    static constexpr int CAP = kStreamPasses * RPP;  // largest tile the consumers cover
+    static constexpr bool ok = RB >= 32 && RB <= 512 && (RB % 32) == 0 && (32 % G) == 0;
+};
+
+// Position in the ring: slot index and the parity of its current use.
+struct RingPos {
+    uint32_t s, ph;
+    __device__ __forceinline__ void next(uint32_t nbuf)
+    {
+        if (++s == nbuf) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(kThreads, kStreamBlocks)
+    k_apply_streamed(ChainParams cp, int B, int nbuf, const T *__restrict__ X, T *__restrict__ Y,
+                     T *__restrict__ R, const T *__restrict__ dinv, PcgScalars ps, Reduce rd)
+{
+    using SL = StreamLayout<T, K>;
+    constexpr int V = SL::V, G = SL::G, RPW = SL::RPW, RPP = SL::RPP, P = kStreamPasses;
+    static_assert(SL::ok, "streamed rows: 32 to 512 bytes");
+    extern __shared__ __align__(128) unsigned char ring_raw[];
+    __shared__ uint32_t sbin[kBinomDim * kBinomDim];
+    __shared__ T tab[1024];
+    __shared__ T red[kWarps][64];
+    __shared__ uint32_t spref[kLowMaxB + 2];
+    __shared__ T s_alpha[64];
+    __shared__ TileMeta<T> s_meta[kWarps];
+    __shared__ __align__(8) uint64_t s_full[kMaxSlots], s_empty[kMaxSlots];
+    __shared__ int s_fail;
+    load_binom(sbin);
+    build_field_tables<T>(tab, cp);
+    if (MODE == kPcgQ && threadIdx.x < K) s_alpha[threadIdx.x] = (T)ps.alpha[threadIdx.x];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nbuf; ++s) {
+            mbar_init(&s_full[s], 1);
+            mbar_init(&s_empty[s], SL::NCW);
+        }
+        s_fail = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int q = 0; q <= B + 1 && q <= kLowMaxB + 1; ++q) {
+            spref[q] = acc;
+            acc += binom(sbin, B, q);
+        }
+    }
+    __syncthreads();
+
+    const int L = cp.L, m = cp.n_up, H = L - B;
+    const uint32_t ntile = 1u << H;
+    const uint32_t rmax = binom(sbin, B, B / 2);
+    const uint32_t slot_elems = rmax * K;
+    T *__restrict__ ring = reinterpret_cast<T *>(ring_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *fail = &s_fail;
+    T part[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) part[v] = (T)0;
+    TileMeta<T> &tm = s_meta[warp];
+    const bool fused_w = (MODE == kPcgQ) && ps.w != nullptr;
+
+    if (warp == kWarps - 1) {
+        // producer
+        RingPos pos{0u, 0u};
+        uint32_t k = 0;
+        bool ok = true;
+        for (uint32_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            const int p = m - __popc(t);
+            if (p < 0 || p > B) continue;  // warp-uniform
+            __syncwarp();
+            tile_meta_warp<T>(sbin, tab, cp, B, t, p, tm);
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t Rt = binom(sbin, B, p), c0 = binom(sbin, B - 1, p);
+                const uint32_t sup = p >= 1 ? binom(sbin, B - 1, p - 1) : 0u;
+                const uint32_t t0 = t & 1u;
+                const uint32_t jcnt = t0 ? c0 : Rt - c0;
+                const int64_t jsrc = t0 ? (int64_t)tm.off - (int64_t)c0 : (int64_t)tm.off + c0 + sup;
+                auto issue = [&](const T *src, uint32_t rows) {
+                    if (!ok) return;
+                    const uint32_t s = pos.s;
+                    // the slot's previous use (one lap ago) must have been released
+                    if (k >= (uint32_t)nbuf && !ring_wait(&s_empty[s], pos.ph ^ 1u, fail)) {
+                        ok = false;
+                        return;
+                    }
+                    fence_proxy_async_smem();
+                    const unsigned bytes = rows * (unsigned)SL::RB;
+                    mbar_arrive_expect_tx(&s_full[s], bytes);
+                    bulk_copy_g2s(ring + (size_t)s * slot_elems, src, bytes, &s_full[s]);
+                    ++k;
+                    pos.next((uint32_t)nbuf);
+                };
+                if (jcnt) issue(X + jsrc * K, jcnt);
+                if (cp.periodic && tm.offper != kNoRow) {
+                    const int p2 = m - __popc(t ^ (1u << (H - 1)));
+                    issue(X + (int64_t)tm.offper * K, binom(sbin, B, p2));
+                }
+                issue(X + (int64_t)tm.off * K, Rt);
+                for (int h = 0; h < tm.nh; ++h) issue(X + ((int64_t)tm.off + (int32_t)tm.shift[h]) * K, Rt);
+                if (MODE == kPcgQ) {
+                    issue(R + (int64_t)tm.off * K, Rt);
+                    if (fused_w) {
+                        issue((const T *)ps.w + (int64_t)tm.off * K, Rt);
+                        issue((const T *)ps.p + (int64_t)tm.off * K, Rt);
+                    }
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        }
+        if (!ok && lane == 0) {
+            // leave no copy in flight: wait (bounded) for the last ring of issued copies
+            const uint32_t k0 = k > (uint32_t)nbuf ? k - (uint32_t)nbuf : 0u;
+            for (uint32_t kk = k0; kk < k; ++kk)
+                mbar_wait_bounded(&s_full[kk % (uint32_t)nbuf], (kk / (uint32_t)nbuf) & 1u);
+        }
+    } else {
+        // consumers: warp w covers rows pp * RPP + w * RPW + lane / G of every tile
+        const int grp = lane / G, col = (lane % G) * V;
+        const T hdelta = cp_half_delta<T>(cp);
+        const LowRec *__restrict__ tbl = g_lowtab + lowtab_base(B);
+        RingPos pos{0u, 0u};
+        bool ok = true;
+        for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+            const int p = m - __popc(t);
+            if (p < 0 || p > B) continue;  // warp-uniform
+            __syncwarp();
+            tile_meta_warp<T>(sbin, tab, cp, B, t, p, tm);
+            __syncwarp();
+            const uint32_t Rt = binom(sbin, B, p), c0 = binom(sbin, B - 1, p);
+            const uint32_t t0 = t & 1u, thi = (t >> (H - 1)) & 1u;
+            const uint32_t jbase = t0 ? 0u : c0, jcnt = t0 ? c0 : Rt - c0;
+            const bool has_wrap = cp.periodic && tm.offper != kNoRow;
+            const uint32_t off = tm.off;
+            const int nh = tm.nh;
+            const T ct = tm.ct;
+            uint32_t jrow[P];
+#pragma unroll
+            for (int pp = 0; pp < P; ++pp) jrow[pp] = (uint32_t)(pp * RPP + warp * RPW + grp);
+            if (ok) {
+                const LowRec *__restrict__ rp = tbl + spref[p];
+                uint4 w0[P], w1[P];
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) {
+                    w0[pp] = make_uint4(0, 0, 0, 0);
+                    w1[pp] = make_uint4(0, 0, 0, 0);
+                    if (jrow[pp] < Rt) {
+                        w0[pp] = __ldg(reinterpret_cast<const uint4 *>(rp + jrow[pp]));
+                        w1[pp] = __ldg(reinterpret_cast<const uint4 *>(rp + jrow[pp]) + 1);
+                    }
+                }
+                T nb[P][V], dx[P][V];
+                T di[P];
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) {
+                    di[pp] = (T)0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        nb[pp][v] = (T)0;
+                        dx[pp][v] = (T)0;
+                    }
+                }
+                // wait for the item at ring position q; false for the whole warp (and the
+                // block flagged) once any lane gave up
+                auto take_at = [&](const RingPos &q, const T *&slot) -> bool {
+                    slot = ring + (size_t)q.s * slot_elems;
+                    return __all_sync(0xffffffffu, ring_wait(&s_full[q.s], q.ph, fail)) != 0;
+                };
+                auto take = [&](const T *&slot) -> bool { return take_at(pos, slot); };
+                auto give = [&]() {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&s_empty[pos.s]);
+                    pos.next((uint32_t)nbuf);
+                };
+                const T *slot = nullptr;
+                if (jcnt) {
+                    if ((ok = take(slot))) {
+#pragma unroll
+                        for (int pp = 0; pp < P; ++pp)
+                            if (jrow[pp] < Rt && jrow[pp] - jbase < jcnt) {
+                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)(jrow[pp] - jbase) * K + col);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
+                            }
+                        give();
+                    }
+                }
+                if (ok && has_wrap) {
+                    if ((ok = take(slot))) {
+#pragma unroll
+                        for (int pp = 0; pp < P; ++pp) {
+                            const uint32_t u = w0[pp].x & 0xffffu;
+                            if (jrow[pp] < Rt && (u & 1u) != thi) {
+                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)(w0[pp].y & 0xffffu) * K + col);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
+                            }
+                        }
+                        give();
+                    }
+                }
+                if (ok) {
+                    if ((ok = take(slot))) {
+#pragma unroll
+                        for (int pp = 0; pp < P; ++pp) {
+                            if (jrow[pp] >= Rt) continue;
+                            const uint32_t j = jrow[pp];
+                            const uint32_t u = w0[pp].x & 0xffffu, cnt = (w0[pp].x >> 16) & 0xffu,
+                                           alow = w0[pp].x >> 24;
+                            const bool join = j - jbase < jcnt;
+                            const bool wrap = has_wrap && (u & 1u) != thi;
+                            const Vec<T, V> x = ldv<T, V>(slot + (int64_t)j * K + col);
+                            const T d = (ct + (tab[u & 255u] + tab[256 + (u >> 8)])) -
+                                        mul_rn(hdelta, (T)(alow + (join ? 1u : 0u) + (wrap ? 1u : 0u)));
+#pragma unroll
+                            for (int v = 0; v < V; ++v) dx[pp][v] = mul_rn(d, x.v[v]);
+                            const uint32_t nbw[6] = {w0[pp].z, w0[pp].w, w1[pp].x, w1[pp].y, w1[pp].z, w1[pp].w};
+#pragma unroll
+                            for (int q = 0; q < 12; ++q) {
+                                if (q >= (int)cnt) break;
+                                const uint32_t jn = (nbw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)jn * K + col);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
+                            }
+                            if (MODE == kPcgQ) di[pp] = dinv[off + j];
+                        }
+                        give();
+                    }
+                }
+                for (int h = 0; h < nh && ok; ++h) {
+                    if ((ok = take(slot))) {
+#pragma unroll
+                        for (int pp = 0; pp < P; ++pp)
+                            if (jrow[pp] < Rt) {
+                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)jrow[pp] * K + col);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
+                            }
+                        give();
+                    }
+                }
+                if (ok) {
+                    T acc[P][V];
+#pragma unroll
+                    for (int pp = 0; pp < P; ++pp)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[pp][v] = fma_rn((T)0.5, nb[pp][v], dx[pp][v]);
+                    if (MODE != kPcgQ) {
+                        const T zero[V] = {};
+#pragma unroll
+                        for (int pp = 0; pp < P; ++pp)
+                            if (jrow[pp] < Rt)
+                                finish_row<T, V, MODE>(acc[pp], 0, off + jrow[pp], Y, K, R, dinv, col, zero, part);
+                    } else {
+                        // r (and w, p) of the tile's rows: items of their own, in that order
+                        const T *sr = nullptr, *sw = nullptr, *sp = nullptr;
+                        ok = take(sr);
+                        if (ok && fused_w) {
+                            RingPos q = pos;
+                            q.next((uint32_t)nbuf);
+                            ok = take_at(q, sw);
+                            q.next((uint32_t)nbuf);
+                            if (ok) ok = take_at(q, sp);
+                        }
+                        if (ok) {
+                            T alpha[V];
+#pragma unroll
+                            for (int v = 0; v < V; ++v) alpha[v] = s_alpha[col + v];
+#pragma unroll
+                            for (int pp = 0; pp < P; ++pp) {
+                                if (jrow[pp] >= Rt) continue;
+                                const int64_t o = (int64_t)jrow[pp] * K + col;
+                                const int64_t g = (int64_t)(off + jrow[pp]) * K + col;
+                                Vec<T, V> rr = ldv<T, V>(sr + o);
+                                const T dd = di[pp];
+#pragma unroll
+                                for (int v = 0; v < V; ++v) {
+                                    rr.v[v] -= alpha[v] * acc[pp][v];
+                                    part[v] += rr.v[v] * (dd * rr.v[v]);
+                                }
+                                stv<T, V>(R + g, rr);
+                                if (fused_w) {
+                                    Vec<T, V> wv = ldv<T, V>(sw + o);
+                                    const Vec<T, V> pv = ldv<T, V>(sp + o);
+#pragma unroll
+                                    for (int v = 0; v < V; ++v) wv.v[v] += alpha[v] * pv.v[v];
+                                    stv<T, V>((T *)ps.w + g, wv);
+                                }
+                            }
+                            give();
+                            if (fused_w) {
+                                give();
+                                give();
+                            }
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                // the ring stopped: this warp's rows of this and every later tile are NaN
+                Vec<T, V> nanv;
+#pragma unroll
+                for (int v = 0; v < V; ++v) nanv.v[v] = (T)NAN;
+                T *dst = (MODE == kPcgQ) ? R : Y;
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp)
+                    if (jrow[pp] < Rt) stv<T, V>(dst + (int64_t)(off + jrow[pp]) * K + col, nanv);
+#pragma unroll
+                for (int v = 0; v < V; ++v) part[v] = (T)NAN;
+            }
+        }
+    }
+    if (MODE == kPlain) return;
+    pcg_block_finish<T, V, G, MODE>(red, part, K, ps, rd);
+}
+
 // Host side of the low-pattern table: built once per tile width and copied to the
 // device table before the first tiled product of that width on the current device.
 static std::mutex g_lowtab_mutex;
@@ -1559,10 +1940,90 @@ static cudaError_t launch_staged_lb(const ChainParams &cp, int Bs, const T *X, T
     return cudaGetLastError();
 }
 
+static bool streamed_schedule(int L, int n_up, int K, size_t es) { return schedule_for(L, n_up, K, es) == 4; }
+
+// Dynamic shared memory a streamed block can have next to the kernel's static arrays.
+template <typename T, int K, int MODE>
+static size_t stream_ring_capacity()
+{
+    static const size_t cap = []() {
+        auto kern = k_apply_streamed<T, K, MODE>;
+        cudaFuncAttributes fa{};
+        int dev = 0, optin = 0, per_sm = 0, reserved = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+            return (size_t)0;
+        // kStreamBlocks blocks share the SM's shared memory
+        size_t block = (size_t)per_sm / kStreamBlocks;
+        block = block > (size_t)reserved ? block - (size_t)reserved : 0;
+        if (block > (size_t)optin) block = (size_t)optin;
+        const size_t avail = block > fa.sharedSizeBytes ? block - fa.sharedSizeBytes : 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail) != cudaSuccess)
+            return (size_t)0;
+        return avail;
+    }();
+    return cap;
+}
+
+// Tile width of the streamed kernel: the widest table-backed B (<= L - 2) whose largest
+// tile the consumer warps cover and whose ring still holds MBL_STREAM_MIN_SLOTS tiles.
+static int stream_bits_for(int L, int K, size_t es, size_t ring_bytes, int cap_rows)
+{
+    int B = kLowMaxB < L - 2 ? kLowMaxB : L - 2;
+    for (; B >= 2; --B) {
+        const size_t rows = host_binom(B, B / 2);
+        if (rows > (size_t)cap_rows) continue;
+        if (ring_bytes / (rows * K * es) >= (size_t)MBL_STREAM_MIN_SLOTS) return B;
+    }
+    return -1;
+}
+
+template <typename T, int K>
+static int stream_bits(int L)
+{
+    using SL = StreamLayout<T, K>;
+    if constexpr (!SL::ok) {
+        return -1;
+    } else {
+        return stream_bits_for(L, K, sizeof(T), stream_ring_capacity<T, K, kPlain>(), SL::CAP);
+    }
+}
+
+template <typename T, int K, int MODE>
+static cudaError_t launch_streamed(const ChainParams &cp, int Bs, const T *X, T *Y, T *R, const T *dinv,
+                                   const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
+{
+    if (ensure_lowtab(Bs) != MBL_OK) return cudaErrorUnknown;
+    const size_t avail = stream_ring_capacity<T, K, MODE>();
+    const size_t slot = (size_t)host_binom(Bs, Bs / 2) * K * sizeof(T);
+    int nbuf = (int)(avail / slot);
+    if (nbuf > kMaxSlots) nbuf = kMaxSlots;
+    if (nbuf < 4) return cudaErrorInvalidConfiguration;
+    const int64_t ntile = (int64_t)1 << (cp.L - Bs);
+    int64_t grid = (int64_t)num_sms() * kStreamBlocks;
+    if (grid > ntile) grid = ntile;
+    note_launch();
+    k_apply_streamed<T, K, MODE><<<(int)grid, kThreads, (size_t)nbuf * slot, st>>>(cp, Bs, nbuf, X, Y, R, dinv, ps,
+                                                                                   rd);
+    return cudaGetLastError();
+}
+
 template <typename T, int K, int MODE>
 static cudaError_t launch_tiled(const ChainParams &cp, int B, const T *X, int64_t ldx, T *Y, int64_t ldy, T *R,
                                 const T *dinv, const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
 {
+    if constexpr (StreamLayout<T, K>::ok) {
+        // streamed: contiguous rows (ld = K) and 16-byte aligned bases for every streamed block
+        auto al = [](const void *q) { return q == nullptr || (uintptr_t)q % 16 == 0; };
+        if (streamed_schedule(cp.L, cp.n_up, K, sizeof(T)) && ldx == K && (Y == nullptr || ldy == K) && al(X) &&
+            al(Y) && al(R) && al(ps.w) && al(ps.p)) {
+            const int Bs = stream_bits<T, K>(cp.L);
+            if (Bs >= 2) return launch_streamed<T, K, MODE>(cp, Bs, X, Y, R, dinv, ps, rd, st);
+        }
+    }
     if constexpr ((K * sizeof(T)) % 16 == 0) {
         // staged: contiguous rows (ld = K) and 16-byte aligned bases for the bulk copies
         const bool aligned = ((uintptr_t)X % 16 == 0) && (Y == nullptr || (uintptr_t)Y % 16 == 0) &&
@@ -1789,9 +2250,48 @@ extern "C" int mbl_set_product_tile_bits(int k, int dtype, int bits)
     return MBL_OK;
 }
 
+// Streamed tile width for a runtime block width (-1: no streamed kernel for it).
+static int stream_bits_k(int L, int k, size_t es)
+{
+    using namespace mbl;
+    if (es == 4) {
+        switch (k) {
+        case 8: return stream_bits<float, 8>(L);
+        case 16: return stream_bits<float, 16>(L);
+        case 32: return stream_bits<float, 32>(L);
+        case 64: return stream_bits<float, 64>(L);
+        default: return -1;
+        }
+    }
+    switch (k) {
+    case 4: return stream_bits<double, 4>(L);
+    case 8: return stream_bits<double, 8>(L);
+    case 16: return stream_bits<double, 16>(L);
+    case 32: return stream_bits<double, 32>(L);
+    case 64: return stream_bits<double, 64>(L);
+    default: return -1;
+    }
+}
+
+extern "C" int mbl_product_tile_width(int L, int dtype, int k, int schedule)
+{
+    using namespace mbl;
+    if ((dtype != MBL_F32 && dtype != MBL_F64) || k < 1 || k > 256 || L < 4 || L > kMaxL || schedule < 1 ||
+        schedule > 4)
+        return MBL_ERR_ARG;
+    const size_t es = dtype == MBL_F32 ? 4 : 8;
+    const bool tiled_k = (k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32 || k == 64);
+    const int B = tiled_k ? tile_bits_for(L, k, es) : -1;
+    if (B < 2) return 0;
+    int w = B;
+    if (schedule == 3) w = (k * (int)es) % 16 == 0 ? staged_bits(L, k, es) : -1;
+    if (schedule == 4) w = stream_bits_k(L, k, es);
+    return w >= 2 ? w : 0;
+}
+
 extern "C" int mbl_set_product_schedule(int k, int dtype, int schedule)
 {
-    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || schedule < 0 || schedule > 3)
+    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || schedule < 0 || schedule > 4)
         return MBL_ERR_ARG;
     mbl::set_schedule(k, dtype == MBL_F32 ? 4 : 8, schedule);
     return MBL_OK;
@@ -1831,10 +2331,13 @@ extern "C" int mbl_autotune_product(const mbl_chain *chain, int dtype, const voi
     float best = -1.0f;
     int best_s = 1, best_l = 32;
     rc = MBL_OK;
-    for (int sch = 1; sch <= 3 && rc == MBL_OK; ++sch) {
+    const int sbits = stream_bits_k(cp.L, k, es);
+    for (int sch = 1; sch <= 4 && rc == MBL_OK; ++sch) {
         if (sch == 3 && (rows % 16 != 0 || staged_bits(cp.L, k, es) < 2)) continue;
+        if (sch == 4 && sbits < 2) continue;
         for (int lane = 32; lane <= 64 && rc == MBL_OK; lane *= 2) {
             if (lane == 64 && rows < 64) continue;  // narrower rows: one lane holds the row either way
+            if (lane == 64 && sch == 4) continue;   // the streamed kernel has one lane width
             t_force_schedule = sch;
             t_force_lane = lane;
             float ms = 0.0f;
@@ -1863,7 +2366,9 @@ extern "C" int mbl_autotune_product(const mbl_chain *chain, int dtype, const voi
     }
     if (choice)
         *choice = mbl_product_choice{best_s, best_l,
-                                     best_s == 3 ? staged_bits(cp.L, k, es) : tile_bits_for(cp.L, k, es),
+                                     best_s == 3   ? staged_bits(cp.L, k, es)
+                                     : best_s == 4 ? sbits
+                                                   : tile_bits_for(cp.L, k, es),
                                      1000.0 * (double)best / reps};
     return MBL_OK;
 }

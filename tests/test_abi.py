@@ -182,12 +182,45 @@ def test_tuning_switches_validate(so):
     for k in (8, 32):
         for dt in (0, 1):
             so.mbl_set_product_lane_bytes(k, dt, 0)
-    for sch, want in ((0, ok), (1, ok), (2, ok), (3, ok), (4, bad), (-1, bad)):
+    for sch, want in ((0, ok), (1, ok), (2, ok), (3, ok), (4, ok), (5, bad), (-1, bad)):
         assert so.mbl_set_product_schedule(64, 0, sch) == want
     so.mbl_set_product_schedule(64, 0, 0)
     for eng, want in ((0, ok), (1, ok), (2, ok), (3, bad), (-1, bad)):
         assert so.mbl_set_gram_engine(eng) == want
     so.mbl_set_gram_engine(0)
+
+
+def test_tile_width_query_host_schedules(so):
+    """mbl_product_tile_width for the host-decided orders: the tile-bits switch for 1 and 2,
+    the widest B <= min(13, L - 2) whose largest tile C(B, B/2) rows fits 48 KB for 3,
+    0 where no tiled kernel exists, MBL_ERR_ARG for bad arguments (no device needed)."""
+    from math import comb
+    from paper_2012_00217_gb300 import binding
+    bad = binding.MBL_ERR_ARG
+    for L, dt, k in ((20, 0, 32), (16, 1, 16), (26, 0, 64), (9, 0, 4)):
+        es = 4 if dt == 0 else 8
+        B = min(13, L - 2)
+        while B >= 2 and comb(B, B // 2) * k * es > 48 * 1024:
+            B -= 1
+        assert so.mbl_product_tile_width(L, dt, k, 3) == B
+        for bits in (5, 9):
+            assert so.mbl_set_product_tile_bits(k, dt, bits) == binding.MBL_OK
+            try:
+                assert so.mbl_product_tile_width(L, dt, k, 1) == min(bits, L - 2)
+                assert so.mbl_product_tile_width(L, dt, k, 2) == min(bits, L - 2)
+            finally:
+                so.mbl_set_product_tile_bits(k, dt, 0)
+        assert so.mbl_product_tile_width(L, dt, k, 1) >= 2
+    assert so.mbl_product_tile_width(20, 0, 3, 1) == 0  # no tiled kernel for k = 3
+    assert so.mbl_product_tile_width(20, 0, 2, 3) == 0  # 8-byte rows: no bulk copies
+    so.mbl_set_product_tile_bits(32, 0, -1)
+    try:
+        assert so.mbl_product_tile_width(20, 0, 32, 3) == 0  # untiled kernel forced
+    finally:
+        so.mbl_set_product_tile_bits(32, 0, 0)
+    for L, dt, k, sch in ((3, 0, 8, 1), (33, 0, 8, 1), (20, 2, 8, 1), (20, 0, 0, 1), (20, 0, 257, 1),
+                          (20, 0, 8, 0), (20, 0, 8, 5)):
+        assert so.mbl_product_tile_width(L, dt, k, sch) == bad
 
 
 def test_autotune_checks_arguments_before_any_launch(so):

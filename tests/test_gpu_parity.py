@@ -288,6 +288,70 @@ def test_staged_schedule_full_size_sampled(mbl):
     assert np.all(np.abs(got - ref) <= 4 * (L + 2) * u * scale + derr * np.abs(Xh).max())
 
 
+@pytest.mark.parametrize("L,periodic,n_up,k,dtype", [
+    (16, True, 8, 32, np.float32), (18, False, 9, 64, np.float32), (14, True, 7, 8, np.float32),
+    (13, False, 5, 16, np.float32), (15, True, 4, 32, np.float32), (20, True, 10, 32, np.float32),
+    (14, False, 7, 32, np.float64), (16, True, 8, 64, np.float64), (12, True, 6, 4, np.float64),
+    (17, True, 8, 16, np.float64), (11, True, 9, 8, np.float64)])
+def test_streamed_schedule_matches_oracle_and_tiled(mbl, L, periodic, n_up, k, dtype):
+    """Schedule 4 (a producer warp streams every row block of a tile's product into a ring
+    of shared-memory slots) against the oracle, and bit for bit against the persistent
+    tiled kernel at the same tile width."""
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    B = mbl.binding.product_tile_width(L, tdt, k, 4)
+    assert B >= 2
+    h = wl.fields(L, 7.0, 200 + L + k)
+    chain = ham.Chain(L, h, delta=1.1, periodic=periodic, n_up=n_up)
+    n = ham.sector_dim(L, n_up)
+    X = wl.block(n, k, 13 + k, dtype)
+    ref = ham.apply(chain, -0.7, X.astype(np.float64))
+    c = mbl.make_chain(L, h, 1.1, periodic, n_up)
+    Xg = _gpu(X)
+    Ys = torch.full((n, k), float("nan"), dtype=tdt, device=DEV)
+    Yt = torch.full((n, k), float("nan"), dtype=tdt, device=DEV)
+    try:
+        mbl.binding.set_product_schedule(k, tdt, 4)
+        mbl.hamiltonian_apply(c, -0.7, Xg, Ys)
+        mbl.binding.set_product_schedule(k, tdt, 1)
+        mbl.binding.set_product_tile_bits(k, tdt, B)
+        mbl.hamiltonian_apply(c, -0.7, Xg, Yt)
+    finally:
+        mbl.binding.set_product_schedule(k, tdt, 0)
+        mbl.binding.set_product_tile_bits(k, tdt, 0)
+    ys = Ys.cpu().numpy()
+    err = np.abs(ys.astype(np.float64) - ref)
+    assert np.all(err <= _bound(chain, -0.7, X, dtype)), err.max()
+    assert np.array_equal(ys, Yt.cpu().numpy())
+
+
+def test_streamed_schedule_full_size_sampled(mbl):
+    """Schedule 4 at L = 26 (k = 32, FP32, periodic): sampled rows against the oracle."""
+    L, k = 26, 32
+    h = wl.fields(L, 8.0, 17)
+    chain = ham.Chain(L, h, periodic=True)
+    n = ham.sector_dim(L, L // 2)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(6)
+    X = torch.randn((n, k), generator=g, device=DEV, dtype=torch.float32)
+    Y = torch.empty_like(X)
+    try:
+        mbl.binding.set_product_schedule(k, torch.float32, 4)
+        mbl.hamiltonian_apply(mbl.make_chain(L, h, 1.0, True), 0.5, X, Y)
+    finally:
+        mbl.binding.set_product_schedule(k, torch.float32, 0)
+    rng = np.random.default_rng(4)
+    rows = np.unique(np.concatenate([rng.integers(0, n, 300), [0, 1, n // 2, n - 2, n - 1]]))
+    Xh = X.cpu().numpy()
+    ref = ham.apply_rows(chain, 0.5, Xh.astype(np.float64), rows)
+    got = Y[torch.from_numpy(rows).to(DEV)].cpu().numpy().astype(np.float64)
+    d = ham.diag(chain)[rows] - 0.5
+    u = np.finfo(np.float32).eps
+    scale = (np.abs(d)[:, None] + 0.5 * L) * np.abs(Xh).max()
+    derr = 6 * u * (np.sum(np.abs(h)) + 0.5 + L)
+    assert np.all(np.abs(got - ref) <= 4 * (L + 2) * u * scale + derr * np.abs(Xh).max())
+    assert torch.isfinite(Y).all()
+
+
 @pytest.mark.parametrize("L,periodic,k,dtype", [(16, True, 32, np.float32), (15, False, 16, np.float64),
                                                 (14, True, 3, np.float32)])
 def test_autotune_keeps_a_correct_choice(mbl, L, periodic, k, dtype):
@@ -304,7 +368,7 @@ def test_autotune_keeps_a_correct_choice(mbl, L, periodic, k, dtype):
     if k == 3:  # no tiled kernel for this width: nothing to choose
         assert choice["schedule"] == 0
     else:
-        assert choice["schedule"] in (1, 2, 3) and choice["lane_bytes"] in (32, 64)
+        assert choice["schedule"] in (1, 2, 3, 4) and choice["lane_bytes"] in (32, 64)
         assert choice["tile_bits"] >= 2 and choice["microseconds"] > 0
     Xh = X.cpu().numpy()
     mbl.hamiltonian_apply(c, 0.25, X, Y)

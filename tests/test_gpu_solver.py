@@ -192,8 +192,10 @@ def test_not_converged_status(mbl):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-def test_staged_schedule_solve_matches_dense(mbl, mode):
-    """The folded LOBPCG with every product (PCG launches included) on schedule 3."""
+@pytest.mark.parametrize("schedule", [3, 4])
+def test_bulk_copy_schedules_solve_matches_dense(mbl, mode, schedule):
+    """The folded LOBPCG with every k = 32 product (PCG launches included) on schedule 3
+    (staged tiles) or 4 (streamed row blocks)."""
     L = 14
     h = wl.fields(L, 8.0, 1)
     ev = np.linalg.eigvalsh(ham.dense_sector(ham.Chain(L, h, periodic=True)))
@@ -202,7 +204,7 @@ def test_staged_schedule_solve_matches_dense(mbl, mode):
     want = np.sort(ev[np.lexsort((ev, np.abs(ev - sigma)))[:16]])
     try:
         for dt in (torch.float32, torch.float64):
-            mbl.binding.set_product_schedule(32, dt, 3)
+            mbl.binding.set_product_schedule(32, dt, schedule)
         evals, resid, stats, vecs = _solve(mbl, L, h, True, sigma, 16, 32, mode, nh, 20, 1)
     finally:
         for dt in (torch.float32, torch.float64):
