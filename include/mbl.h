@@ -149,13 +149,14 @@ int mbl_product_tile_width(int L, int dtype, int k, int schedule);
  * product of this chain, block width k, type dtype, under every candidate -- schedule
  * persistent / ordered / staged / streamed (where its conditions hold) times 32- or
  * 64-byte lanes (64 only for rows of >= 64 bytes; streamed has one lane width) -- on the
- * caller's buffers X_dev, Y_dev (n x k,
- * ld = k, n = C(L, n_up); X is read, Y overwritten; they must not overlap): one warm-up
- * and `reps` timed launches each (1 <= reps <= 1000), CUDA events on `stream`.  The
- * fastest is kept for all later products with this L, k and dtype in this process (the
- * explicit switches above still take precedence) and reported in *choice (optional):
- * schedule 1..4, lane bytes, tile bits and the mean microseconds per product.  Widths k
- * without a tiled kernel leave nothing to choose: MBL_OK with *choice zeroed.
+ * caller's buffers X_dev, Y_dev (n x k, ld = k, n = C(L, n_up); X is read, Y
+ * overwritten; they must not overlap): one warm-up and `reps` timed launches each
+ * (1 <= reps <= 1000), CUDA events on `stream`.  The fastest is kept -- the size-based
+ * default of mbl_set_product_schedule unless another candidate is more than 2 % faster
+ * -- for all later products with this L, k and dtype in this process (the explicit
+ * switches above still take precedence) and reported in *choice (optional): schedule
+ * 1..4, lane bytes, tile bits and the mean microseconds per product.  Widths k without a
+ * tiled kernel leave nothing to choose: MBL_OK with *choice zeroed.
  * Host-synchronous (waits for its timing launches). */
 typedef struct {
     int schedule;

@@ -1853,6 +1853,14 @@ static thread_local int t_force_schedule = 0, t_force_lane = 0;
 // The staged schedule (whole tiles in shared memory) is the default for 128-byte rows
 // once the block vector outgrows 16 MB (measured: 2-6 % faster there, slower for
 // narrower and wider rows); anything else defaults to persistent.
+static int size_schedule(int L, int n_up, int K, size_t es)
+{
+    const double bytes = (double)host_binom(L, n_up) * K * (double)es;
+    if (K * (int)es >= 256 && bytes >= (es == 8 ? 128.0 * (1 << 20) : 1024.0 * (1 << 20))) return 2;
+    if (K * (int)es == 128 && bytes >= 16.0 * (1 << 20)) return 3;
+    return 1;
+}
+
 static int schedule_for(int L, int n_up, int K, size_t es)
 {
     if (t_force_schedule) return t_force_schedule;
@@ -1860,15 +1868,14 @@ static int schedule_for(int L, int n_up, int K, size_t es)
     if (o) return o;
     const int a = (L >= 0 && L <= kMaxL) ? g_tuned[es == 8 ? 1 : 0][kslot(K)][L].schedule : 0;
     if (a) return a;
-    const double bytes = (double)host_binom(L, n_up) * K * (double)es;
-    if (K * (int)es >= 256 && bytes >= (es == 8 ? 128.0 * (1 << 20) : 1024.0 * (1 << 20))) return 2;
-    if (K * (int)es == 128 && bytes >= 16.0 * (1 << 20)) return 3;
-    return 1;
+    return size_schedule(L, n_up, K, es);
 }
 static bool ordered_schedule(int L, int n_up, int K, size_t es) { return schedule_for(L, n_up, K, es) == 2; }
 
 // 32-byte lanes by default; 64-byte lanes for FP64 rows of >= 128 bytes (measured 13 %
 // faster: the FP64 products are ALU-bound and wider lanes repeat less index work).
+static int size_lane_bytes(int K, size_t es) { return (es == 8 && K * (int)es >= 128) ? 64 : 32; }
+
 static int lane_bytes_for(int L, int K, size_t es)
 {
     if (t_force_lane) return t_force_lane;
@@ -1876,7 +1883,7 @@ static int lane_bytes_for(int L, int K, size_t es)
     if (v == 16 || v == 32 || v == 64) return v;
     const int a = (L >= 0 && L <= kMaxL) ? g_tuned[es == 8 ? 1 : 0][kslot(K)][L].lane : 0;
     if (a) return a;
-    return (es == 8 && K * (int)es >= 128) ? 64 : 32;
+    return size_lane_bytes(K, es);
 }
 
 template <typename T, int K, int MODE, int LB>
@@ -2328,8 +2335,10 @@ extern "C" int mbl_autotune_product(const mbl_chain *chain, int dtype, const voi
         return MBL_ERR_CUDA;
     }
     const int rows = (int)(k * es);
-    float best = -1.0f;
+    float best = -1.0f, def_ms = -1.0f;
     int best_s = 1, best_l = 32;
+    // the size-based default, kept unless a candidate beats it by more than timing noise
+    const int def_s = size_schedule(cp.L, cp.n_up, k, es), def_l = rows >= 64 ? size_lane_bytes(k, es) : 32;
     rc = MBL_OK;
     const int sbits = stream_bits_k(cp.L, k, es);
     for (int sch = 1; sch <= 4 && rc == MBL_OK; ++sch) {
@@ -2355,7 +2364,13 @@ extern "C" int mbl_autotune_product(const mbl_chain *chain, int dtype, const voi
                 best_s = sch;
                 best_l = lane;
             }
+            if (rc == MBL_OK && sch == def_s && lane == def_l) def_ms = ms;
         }
+    }
+    if (rc == MBL_OK && def_ms > 0.0f && best > 0.98f * def_ms) {
+        best = def_ms;
+        best_s = def_s;
+        best_l = def_l;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
