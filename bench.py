@@ -439,7 +439,8 @@ def run_reference(args):
 
 def run_profile(args):
     """Small fixed workloads for ncu: 'product' launches the L = 20 (k = 32) and L = 26
-    (k = 64) FP32 block products three times each; 'pcg' runs a 3-iteration solve;
+    (k = 64) FP32 block products three times each; 'pcg' runs the bench solve for two
+    LOBPCG iterations of 30 PCG steps each, graphs on (the kernels of a step, ~300 launches);
     'bounds' runs the spectrum bounds of the bench workload once; 'gram' runs the
     tensor-core Gram at n = 184,756 (96 x 96) and n = 705,432 (192 x 192) twice each."""
     import torch
@@ -478,8 +479,8 @@ def run_profile(args):
     else:
         s = _setup(torch, mbl, dev)
         step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
-        step.opts.max_iter = 3
-        step.opts.use_graph = 0
+        step.opts.max_iter = 2
+        step.opts.pcg_iters = 30
         mbl.basis_build(s["L"], s["L"] // 2, step.states)
         emin, emax, _ = -37.11044143972399, 33.466977761420935, 0
         step.opts.norm_h = max(abs(emin), abs(emax))
@@ -498,7 +499,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the sweep, the batch and the CPU baseline")
     ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
-                         "FP32) or a 3-iteration solve, for an ncu capture")
+                         "FP32), a short solve (2 iterations x 30 PCG steps), the spectrum bounds or the "
+                         "tensor-core Grams, for an ncu capture")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -601,7 +603,8 @@ def main():
                      "frac": kern["gbs_warm"] / peaks["hbm_gbs"],
                      "traffic": profiled_traffic("L20_k32_f32"),
                      "kernel": kern["kernel"] + " under the autotuned schedule %d (1 persistent, 2 ordered, 3 "
-                               "staged), algorithmic 2nk*4 B per launch / CUDA-event launch time" % tuned["f32"]["schedule"],
+                               "staged, 4 streamed), algorithmic 2nk*4 B per launch / CUDA-event launch time"
+                               % tuned["f32"]["schedule"],
                      "peak_kind": peak_kind + " (hbm_gbs)"},
         "matvec_roofline": None,
         "solve_kernel": kern,
