@@ -48,7 +48,8 @@ BOUNDS_TOL = 1e-7
 
 
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "product_kernel_l20_l26.md")
-PRODUCT_SOURCE = os.path.join(ROOT, "paper_2012_00217_gb300", "csrc", "mbl_apply.cu")
+# the sources the product kernels are compiled from (the summary's SHA-1 covers both, in order)
+PRODUCT_SOURCES = [os.path.join(ROOT, "paper_2012_00217_gb300", "csrc", f) for f in ("mbl_apply.cu", "mbl_device.cuh")]
 # 240 PCG steps per LOBPCG iteration: 39 eigenpairs/s on this sample against 27 at 80
 # and 38 at 320 (fewer, longer inner solves, as for the L = 20 step)
 BATCH_SAMPLE = dict(W=(2.0, 4.0, 8.0), per_w=dict(L16=10, L14=3, L18=3), nev=8, k=16, pcg_iters=240)
@@ -86,7 +87,7 @@ def profiled_traffic(key):
     when the summary is absent or the kernel source has changed since it was taken."""
     try:
         text = open(PROFILE_SUMMARY).read()
-        sha = hashlib.sha1(open(PRODUCT_SOURCE, "rb").read()).hexdigest()
+        sha = hashlib.sha1(b"".join(open(f, "rb").read() for f in PRODUCT_SOURCES)).hexdigest()
     except OSError:
         return None
     src, val = None, None

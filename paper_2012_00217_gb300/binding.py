@@ -393,7 +393,8 @@ def bounds_workspace_size(chain, k):
 
 
 def spectrum_bounds(chain, X0, workspace, tol=1e-10, max_iter=500):
-    """(E_min, E_max, iterations) by LOBPCG on +H and -H from the n x k block X0."""
+    """(E_min, E_max, Lanczos steps): mbl_spectrum_bounds, one FP64 Lanczos recurrence on H
+    started from column 0 of the n x k block X0."""
     torch = _torch()
     emin, emax, iters = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     _check(lib().mbl_spectrum_bounds(ctypes.byref(chain), X0.shape[1], float(tol), int(max_iter),

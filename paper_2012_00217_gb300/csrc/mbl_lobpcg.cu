@@ -1,5 +1,6 @@
 // mbl_lobpcg.cu -- folded-spectrum LOBPCG with a Jacobi-PCG preconditioner (Sec. 3.2,
-// Sec. 6.2), and the spectrum-bounds LOBPCG on +H / -H used to place sigma.
+// Sec. 6.2), and the ABI entries of the spectrum bounds used to place sigma (the Lanczos
+// recurrence itself is in mbl_lanczos.cu).
 //
 // One iteration (every product of H runs in the gather kernels of mbl_apply.cu; every
 // reduction is deterministic):

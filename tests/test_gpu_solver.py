@@ -152,7 +152,8 @@ def test_mixed_and_fp64_agree_l18(mbl):
     assert abs(s64["iters"] - s32["iters"]) <= max(3, s64["iters"] // 5)
 
 
-def test_spectrum_bounds_match_dense_and_oracle(mbl):
+def test_spectrum_bounds_match_dense(mbl):
+    """The FP64 Lanczos bounds (both ends from one recurrence) against dense LAPACK."""
     L = 14
     h = wl.fields(L, 8.0, 4)
     ev = np.linalg.eigvalsh(ham.dense_sector(ham.Chain(L, h, periodic=True)))
