@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(
     if (MODE == kPlain) {
         // ordered schedule (at most one item per warp): a block whose items hold no rows
         // leaves before any setup
-        const uint32_t nch = (c_binom.v[B * kBinomDim + B / 2] + CH - 1) / CH;
+        const uint32_t nch = (__ldg(&g_binom.v[B * kBinomDim + B / 2]) + CH - 1) / CH;
         const uint32_t tot = (1u << (cp.L - B)) * nch;
         if ((uint64_t)gridDim.x * kWarps >= tot) {
             int any = 0;
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(
                 if (item < tot) {
                     const uint32_t t = item / nch, c = item % nch;
                     const int p = cp.n_up - __popc(t);
-                    any = (p >= 0 && p <= B && c * CH < c_binom.v[B * kBinomDim + p]) ? 1 : 0;
+                    any = (p >= 0 && p <= B && c * CH < __ldg(&g_binom.v[B * kBinomDim + p])) ? 1 : 0;
                 }
             }
             if (!__syncthreads_or(any)) return;

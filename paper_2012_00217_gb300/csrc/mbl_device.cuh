@@ -32,13 +32,16 @@ constexpr BinomTable make_binom_table()
 }
 
 // C(32, 16) = 601,080,390 < 2^32, so every entry fits in uint32.  One copy per
-// translation unit (no relocatable device code needed).
-static __constant__ BinomTable c_binom = make_binom_table();
+// translation unit (no relocatable device code needed), in global memory: blocks copy it
+// into shared memory with consecutive threads reading consecutive words (from L2 after
+// the first launch).  From constant memory that copy cost ~3 us per product launch at
+// L = 20: the constant cache serves the 32 different addresses of a warp one at a time.
+static __device__ const BinomTable g_binom = make_binom_table();
 
 // Copy the binomial table into shared memory (call with all threads, then sync).
 __device__ __forceinline__ void load_binom(uint32_t *sb)
 {
-    for (int i = threadIdx.x; i < kBinomDim * kBinomDim; i += blockDim.x) sb[i] = c_binom.v[i];
+    for (int i = threadIdx.x; i < kBinomDim * kBinomDim; i += blockDim.x) sb[i] = __ldg(&g_binom.v[i]);
 }
 
 __device__ __forceinline__ uint32_t binom(const uint32_t *sb, int i, int j)
