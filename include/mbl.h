@@ -127,8 +127,8 @@ int mbl_set_product_lane_bytes(int k, int dtype, int bytes);
  * (plain products only: one chunk of rows per warp; the hardware dispatches blocks in
  * index order, so the tiles being read advance as a narrow window that stays in L2),
  * 3 = staged (each block copies whole tiles of at most 48 KB into shared memory with bulk
- * asynchronous copies and reads the in-tile neighbours there), 4 = streamed (one block per
- * SM; a producer warp copies every row block a tile's product reads -- joining-bond
+ * asynchronous copies and reads the in-tile neighbours there), 4 = streamed (two blocks
+ * per SM; a producer warp copies every row block a tile's product reads -- joining-bond
  * partners, wrap partner tile, the tile, one block per antiparallel high bond, and for the
  * PCG launches the rows of r, w, p -- into a ring of shared-memory slots with bulk
  * asynchronous copies, and the other warps add them up; rows of 32 to 512 bytes).  3 and
