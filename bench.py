@@ -350,7 +350,33 @@ def batched_sample(torch, mbl, dev, nstreams=16):
     return dict(value=len(chains) * nev / t, unit="eigenpairs/s", seconds=t, problems=len(chains), nev=nev, k=k,
                 streams=nstreams, pcg_iters=BATCH_SAMPLE["pcg_iters"], iters_mean=float(np.mean(its)),
                 iters_max=int(max(its)), max_rel_resid=float(max(st["max_rel_resid"] for st in stats)),
-                sample="per W in {2,4,8}: seeds 0-9 (L=16), 256-258 (L=14), 320-322 (L=18), open chains")
+                sample="per W in {2,4,8}: seeds 0-9 (L=16), 256-258 (L=14), 320-322 (L=18), open chains",
+                gap_ratio=gap_ratio_by_w(torch, mbl, dev, ev, len(pick)))
+
+
+def gap_ratio_by_w(torch, mbl, dev, ev, per_w):
+    """Adjacent gap ratio (Sec. 2.2) of the batch's converged levels on the GPU: the mean
+    ratio per disorder strength (ratios pooled over that W's problems) and the time of
+    the call for the whole batch (CUDA events around it, so host-side call overhead is
+    included).  With 8 levels (6 ratios) per problem the sample
+    is small; it shows the indicator running on the solver's output, not a converged
+    statistic."""
+    E = torch.from_numpy(np.ascontiguousarray(ev, dtype=np.float64)).to(dev)
+    st = torch.cuda.current_stream()
+    mbl.gap_ratio(E)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    r, c = mbl.gap_ratio(E)
+    e1.record(st)
+    e1.synchronize()
+    r, c = r.cpu().numpy(), c.cpu().numpy()
+    out = {}
+    for i, W in enumerate(BATCH_SAMPLE["W"]):
+        rr, cc = r[i * per_w:(i + 1) * per_w], c[i * per_w:(i + 1) * per_w]
+        ok = cc > 0
+        out["W=%g" % W] = float((rr[ok] * cc[ok]).sum() / cc[ok].sum()) if ok.any() else None
+    out.update(ratios=int(c.sum()), problems=int(E.shape[0]), call_us=e0.elapsed_time(e1) * 1e3)
+    return out
 
 
 def config_l26_iterations(torch, mbl, dev, iters=2):

@@ -301,6 +301,22 @@ int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, int max_iter,
                         double *emin_host, double *emax_host, int *iters_host,
                         mbl_stream_t stream);
 
+/* ---- localization indicators (Sec. 2.2) ------------------------------------------- */
+
+/* Adjacent gap ratio of converged eigenvalues (Sec. 2.2, in the form of the work it cites):
+ * for each of nprob disorder realizations, its m levels evals_dev[i * ld + 0 .. m-1] (FP64
+ * device memory, any order) are sorted; with the gaps d_j = E_{j+1} - E_j, every interior
+ * level j = 1 .. m-2 gives r_j = min(d_{j-1}, d_j) / max(d_{j-1}, d_j), and a level whose
+ * two gaps are both zero is skipped.  Writes r_mean_dev[i] (FP64 device memory) = the mean
+ * of realization i's ratios, and count_dev[i] (int32 device memory) = their number; NaN
+ * and 0 when it has none (m < 3) or when one of its levels is not finite.  The mean over
+ * several realizations is sum(r_mean * count) / sum(count) (skip count 0).  One block per
+ * realization on `stream`; fixed-order sums, bitwise reproducible.  Returns MBL_ERR_ARG
+ * (nothing launched) for nprob < 0, m outside 1..4096, ld < m or a null pointer with
+ * nprob > 0; nprob = 0 is a no-op. */
+int mbl_gap_ratio(int nprob, int m, const double *evals_dev, int64_t ld, double *r_mean_dev,
+                  int *count_dev, mbl_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

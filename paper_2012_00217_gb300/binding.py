@@ -34,7 +34,7 @@ EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis
             "mbl_set_product_tile_bits", "mbl_set_product_lane_bytes", "mbl_batched_workspace_size",
             "mbl_lobpcg_solve_batched", "mbl_kernel_launch_count",
             "mbl_set_product_schedule", "mbl_autotune_product", "mbl_set_gram_engine",
-            "mbl_gram_workspace_size", "mbl_gram", "mbl_product_tile_width")
+            "mbl_gram_workspace_size", "mbl_gram", "mbl_product_tile_width", "mbl_gap_ratio")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -104,6 +104,8 @@ def lib():
     so.mbl_set_product_schedule.argtypes = [i32, i32, i32]
     so.mbl_product_tile_width.restype = i32
     so.mbl_product_tile_width.argtypes = [i32, i32, i32, i32]
+    so.mbl_gap_ratio.restype = i32
+    so.mbl_gap_ratio.argtypes = [i32, i32, p, i64, p, p, p]
     so.mbl_set_gram_engine.restype = i32
     so.mbl_set_gram_engine.argtypes = [i32]
     so.mbl_gram_workspace_size.restype = i32
@@ -402,3 +404,19 @@ def spectrum_bounds(chain, X0, workspace, tol=1e-10, max_iter=500):
                                      workspace.numel(), ctypes.byref(emin), ctypes.byref(emax),
                                      ctypes.byref(iters), _stream_ptr(X0)), "mbl_spectrum_bounds")
     return emin.value, emax.value, iters.value
+
+
+def gap_ratio(evals, m=None):
+    """mbl_gap_ratio on the rows of a 2-D float64 CUDA tensor (one realization per row,
+    its first m entries the levels): returns (r_mean float64, count int32) CUDA tensors."""
+    torch = _torch()
+    if evals.dim() != 2 or evals.dtype != torch.float64 or not evals.is_cuda or evals.stride(1) != 1:
+        raise ValueError("evals: 2-D float64 CUDA tensor with unit column stride")
+    nprob, ld = evals.shape[0], evals.stride(0) if evals.shape[0] > 1 else evals.shape[1]
+    m = evals.shape[1] if m is None else int(m)
+    r_mean = torch.empty(nprob, dtype=torch.float64, device=evals.device)
+    count = torch.empty(nprob, dtype=torch.int32, device=evals.device)
+    _check(lib().mbl_gap_ratio(int(nprob), m, ctypes.c_void_p(evals.data_ptr()), int(ld),
+                               ctypes.c_void_p(r_mean.data_ptr()), ctypes.c_void_p(count.data_ptr()),
+                               _stream_ptr(evals)), "mbl_gap_ratio")
+    return r_mean, count

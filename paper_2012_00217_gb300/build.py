@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libmbl_gb300.so")
 SOURCES = ["mbl_basis.cu", "mbl_apply.cu", "mbl_dense.cu", "mbl_gram_tc.cu", "mbl_small.cu", "mbl_lanczos.cu",
-           "mbl_lobpcg.cu"]
+           "mbl_lobpcg.cu", "mbl_observables.cu"]
 HEADERS = ["mbl_device.cuh", "mbl_internal.h", "mbl_dense.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",

@@ -236,6 +236,17 @@ def test_autotune_checks_arguments_before_any_launch(so):
         assert rc == binding.MBL_ERR_ARG  # the last case: X and Y overlap
 
 
+def test_gap_ratio_checks_arguments_before_any_launch(so):
+    from paper_2012_00217_gb300 import binding
+    ok, bad = binding.MBL_OK, binding.MBL_ERR_ARG
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every case fails its checks or launches nothing
+    for nprob, m, ld, ptrs, want in ((-1, 8, 8, (fake, fake, fake), bad), (4, 0, 8, (fake, fake, fake), bad),
+                                     (4, 4097, 4097, (fake, fake, fake), bad), (4, 8, 7, (fake, fake, fake), bad),
+                                     (4, 8, 8, (None, fake, fake), bad), (4, 8, 8, (fake, None, fake), bad),
+                                     (4, 8, 8, (fake, fake, None), bad), (0, 8, 8, (None, None, None), ok)):
+        assert so.mbl_gap_ratio(nprob, m, ptrs[0], ld, ptrs[1], ptrs[2], None) == want
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2012_00217_gb300 import binding
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "absent.so"))
