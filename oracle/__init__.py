@@ -11,5 +11,6 @@ Modules:
                  Rayleigh-Ritz with H, spectrum bounds (Sec. 3.2, Sec. 6.2).
   closed_form -- Jordan-Wigner free-fermion spectrum at delta = 0 and other
                  closed forms used to pin the above.
-  observables -- the adjacent gap ratio of converged eigenvalues (Sec. 2.2).
+  observables -- the adjacent gap ratio of converged eigenvalues and the
+                 half-chain entanglement entropy of eigenvectors (Sec. 2.2).
 """

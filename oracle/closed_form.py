@@ -10,6 +10,13 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   periodic chain the wrap-around hop carries the fermion-parity sign (-1)^(N-1).
 * ``trace_h`` -- Tr H over the sector: the field terms average to h_i (2N-L)/L and a
   bond's z_i z_j averages to 1 - 4N(L-N)/(L(L-1)) over the C(L, N) states.
+* ``free_fermion_entropy`` -- the entanglement entropy of the first l_a sites in an
+  eigenstate of the open delta = 0 chain, from its single-particle modes alone (the
+  correlation-matrix method of Peschel, 2003): with C_ij = sum over occupied modes k of
+  phi_k(i) phi_k(j) restricted to the first l_a sites and its eigenvalues nu,
+  S = -sum [nu ln nu + (1 - nu) ln (1 - nu)].  The Jordan-Wigner string of a site in the
+  left block only involves sites of that block, so the spin and fermion reduced states
+  agree.
 """
 import itertools
 
@@ -67,3 +74,20 @@ def trace_h(L, h, delta, n_up, periodic, n):
     zz = 1.0 - 4.0 * n_up * (L - n_up) / (L * (L - 1.0))
     z = (2.0 * n_up - L) / L
     return n * (0.25 * delta * nb * zz + 0.5 * float(np.sum(h)) * z)
+
+
+def free_fermion_entropy(L, h, occupied, l_a):
+    """(energy, entropy of sites 0..l_a-1) of the open delta = 0 eigenstate that fills the
+    single-particle modes ``occupied`` (indices into the ascending single-particle levels)."""
+    T = hopping_matrix(L, h, len(occupied), False)
+    eps, phi = np.linalg.eigh(T)
+    occ = list(occupied)
+    energy = float(np.sum(eps[occ]) - 0.5 * np.sum(h))
+    C = phi[:l_a, occ] @ phi[:l_a, occ].T
+    nu = np.clip(np.linalg.eigvalsh(C), 0.0, 1.0)
+    ent = 0.0
+    for v in nu:
+        for q in (v, 1.0 - v):
+            if q > 1e-300:
+                ent -= q * np.log(q)
+    return energy, float(ent)

@@ -67,3 +67,76 @@ def test_model_trend_weak_vs_strong_disorder():
         return obs.gap_ratio_average(reals)
     weak, strong = mean_r(0.5, range(6)), mean_r(12.0, range(6))
     assert weak > 0.48 and strong < 0.43 and weak - strong > 0.08
+
+
+# ---------------------------------------------------------------- entanglement entropy
+def _word(up_sites):
+    return sum(1 << i for i in up_sites)
+
+
+def _vec(states, amp):
+    v = np.zeros(states.size)
+    for word, a in amp.items():
+        v[int(np.searchsorted(states, word))] = a
+    return v
+
+
+def test_entropy_of_product_states_is_zero():
+    st = ham.basis(10, 5)
+    for r in (0, 17, st.size - 1):
+        v = np.zeros(st.size)
+        v[r] = 1.0
+        for l_a in (1, 4, 5, 9):
+            assert obs.entanglement_entropy(st, v, l_a) == 0.0
+
+
+def test_entropy_of_singlets_across_the_cut():
+    st = ham.basis(10, 5)
+    base = _word([0, 1, 6, 7])
+    # one singlet on the bond (4, 5) that the cut after 5 sites crosses: ln 2
+    v = _vec(st, {base | _word([4]): 1.0, base | _word([5]): -1.0})
+    assert obs.entanglement_entropy(st, v, 5) == pytest.approx(math.log(2), abs=1e-14)
+    # the same vector cut after 3 sites: the singlet is on the right, S = 0
+    assert obs.entanglement_entropy(st, v, 3) == pytest.approx(0.0, abs=1e-14)
+    # two singlets (4, 5) and (3, 6) crossing the cut: 2 ln 2 (sign and norm do not matter)
+    b2 = _word([0, 1, 7])
+    amp = {}
+    for a, sa in (((4,), 1.0), ((5,), -1.0)):
+        for b, sb in (((3,), 1.0), ((6,), -1.0)):
+            amp[b2 | _word(a + b)] = 3.0 * sa * sb
+    v2 = _vec(st, amp)
+    assert obs.entanglement_entropy(st, -v2, 5) == pytest.approx(2 * math.log(2), abs=1e-13)
+
+
+@pytest.mark.parametrize("L,l_a", [(10, 5), (10, 3), (12, 6), (12, 7)])
+def test_entropy_matches_free_fermion_closed_form(L, l_a):
+    # delta = 0, open chain: eigenstates are Slater determinants; the dense eigenvector of
+    # the matching energy must carry the correlation-matrix entropy of its modes
+    from oracle import closed_form as cf
+    rng = np.random.default_rng(L + 10 * l_a)
+    h = rng.uniform(-2.0, 2.0, L)
+    n_up = L // 2
+    st = ham.basis(L, n_up)
+    ev, V = np.linalg.eigh(ham.dense_sector(ham.Chain(L, h, delta=0.0)))
+    checked = 0
+    for trial in range(12):
+        occ = sorted(rng.choice(L, n_up, replace=False)) if trial else list(range(n_up))
+        E, S = cf.free_fermion_entropy(L, h, occ, l_a)
+        j = int(np.argmin(np.abs(ev - E)))
+        gaps = np.abs(np.delete(ev, j) - ev[j])
+        if abs(ev[j] - E) > 1e-10 or gaps.min() < 1e-6:
+            continue  # degenerate within the tolerance: no unique eigenvector to compare
+        assert obs.entanglement_entropy(st, V[:, j], l_a) == pytest.approx(S, abs=1e-9)
+        checked += 1
+    assert checked >= 6
+
+
+def test_entropy_bounded_by_the_reduced_rank():
+    from math import comb
+    rng = np.random.default_rng(5)
+    L, l_a = 12, 6
+    st = ham.basis(L, 6)
+    rank = sum(min(comb(l_a, p), comb(L - l_a, 6 - p)) for p in range(0, 7))
+    for _ in range(3):
+        S = obs.entanglement_entropy(st, rng.normal(size=st.size), l_a)
+        assert 0.0 < S <= math.log(rank) + 1e-12
