@@ -323,6 +323,25 @@ def solve_kernel_roofline(torch, mbl, dev, s, peak_gbs):
                 t_cold_us=t_cold * 1e6, gbs_cold=alg / t_cold / 1e9, gbs_warm=alg / t_warm / 1e9)
 
 
+def entropy_of_step(torch, mbl, s, step):
+    """Half-chain entanglement entropy (Sec. 2.2) of the step's 16 converged eigenvectors
+    (L = 20, cut after 10 sites): their mean and range, and the call's CUDA-event time
+    (one warm-up call first; the workspace is allocated outside the timed call)."""
+    L = s["L"]
+    ws = torch.empty(mbl.binding.entanglement_workspace_size(s["chain"], L // 2, s["nev"]), dtype=torch.uint8,
+                     device=step.evecs.device)
+    mbl.entanglement_entropy(s["chain"], L // 2, step.evecs, ws)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    S = mbl.entanglement_entropy(s["chain"], L // 2, step.evecs, ws)
+    e1.record(st)
+    e1.synchronize()
+    S = S.cpu().numpy()
+    return dict(cut=L // 2, vectors=int(S.size), mean=float(S.mean()), min=float(S.min()), max=float(S.max()),
+                ms=e0.elapsed_time(e1), workspace_mb=ws.numel() / 1e6)
+
+
 def batched_sample(torch, mbl, dev, nstreams=16):
     """Disorder averaging (uneven L, several W): a bounded sample of the 352-problem
     batch -- per W in {2, 4, 8}: 10 x L=16, 3 x L=14, 3 x L=18 (the first seeds of each
@@ -592,6 +611,7 @@ def main():
     step.run()
     step.opts.timing = 0
     phases = {kk: v for kk, v in step.last["stats"].items() if kk.startswith("t_")}
+    ent = entropy_of_step(torch, mbl, s, step)
     kern = solve_kernel_roofline(torch, mbl, dev, s, peaks["hbm_gbs"])
     sweep = [] if args.quick else matvec_roofline(torch, mbl, dev, peaks["hbm_gbs"])
     big = [r for r in sweep if r["L"] == 26 and r["k"] == 64 and r["dtype"] == "f32"]
@@ -638,6 +658,7 @@ def main():
         "autotuned": tuned,
         "solve_phases_s": phases,
         "bounds_s": t_b,
+        "entanglement": ent,
         "batched": batch,
         "l26_periodic_k64": l26,
         "matvec_sweep": sweep,

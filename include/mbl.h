@@ -317,6 +317,25 @@ int mbl_spectrum_bounds(const mbl_chain *chain, int k, double tol, int max_iter,
 int mbl_gap_ratio(int nprob, int m, const double *evals_dev, int64_t ld, double *r_mean_dev,
                   int *count_dev, mbl_stream_t stream);
 
+/* Half-chain entanglement entropy of sector vectors (Sec. 2.2): the chain is cut after
+ * its first l_a sites (1 <= l_a <= L - 1) and S = -sum lambda ln lambda over the
+ * eigenvalues lambda of the reduced density matrix of sites 0 .. l_a-1, for each of the
+ * nvec columns of V_dev (n x nvec, row-major, ld ldv >= nvec, FP64 device memory,
+ * n = C(L, n_up) rows in the basis order of mbl_basis_build; a column need not be
+ * normalised: lambda is taken relative to its squared norm).  The reduced density matrix
+ * is the direct sum over p (up spins on the left) of M_p M_p^T, M_p holding the column's
+ * entries with p up spins on the left (rows: left patterns, columns: right patterns); its
+ * eigenvalues come from the smaller Gram of each M_p by FP64 Jacobi.  Writes S_dev[nvec]
+ * (FP64 device memory; NaN for a zero column).  chain->h, delta and periodic are not used.
+ * Limit: every Gram side min(C(l_a, p), C(L - l_a, n_up - p)) <= 512 (the half cut up to
+ * L = 22), else MBL_ERR_ARG.  Workspace: mbl_entanglement_workspace_size bytes of device
+ * memory (about 1 MB per column and p at L = 20, l_a = 10).  Deterministic (fixed-order
+ * sums).  Runs on `stream`; nvec = 0 is a no-op. */
+int mbl_entanglement_workspace_size(const mbl_chain *chain, int l_a, int nvec, size_t *bytes);
+int mbl_entanglement_entropy(const mbl_chain *chain, int l_a, int nvec, const double *V_dev, int64_t ldv,
+                             double *S_dev, void *workspace_dev, size_t workspace_bytes,
+                             mbl_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

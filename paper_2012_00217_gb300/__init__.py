@@ -6,5 +6,6 @@ marshalling layer.  PyTorch supplies device memory and streams only.
 """
 from . import binding  # noqa: F401
 from .binding import (MODE_FP64, MODE_MIXED, MBLError, basis_build, basis_rank,  # noqa: F401
-                      basis_size, bounds_workspace_size, gap_ratio, hamiltonian_apply, lobpcg_solve,
+                      basis_size, bounds_workspace_size, entanglement_entropy, gap_ratio,
+                      hamiltonian_apply, lobpcg_solve,
                       lobpcg_workspace_size, make_chain, make_opts, spectrum_bounds)

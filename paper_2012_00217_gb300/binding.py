@@ -34,7 +34,8 @@ EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis
             "mbl_set_product_tile_bits", "mbl_set_product_lane_bytes", "mbl_batched_workspace_size",
             "mbl_lobpcg_solve_batched", "mbl_kernel_launch_count",
             "mbl_set_product_schedule", "mbl_autotune_product", "mbl_set_gram_engine",
-            "mbl_gram_workspace_size", "mbl_gram", "mbl_product_tile_width", "mbl_gap_ratio")
+            "mbl_gram_workspace_size", "mbl_gram", "mbl_product_tile_width", "mbl_gap_ratio",
+            "mbl_entanglement_workspace_size", "mbl_entanglement_entropy")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -106,6 +107,10 @@ def lib():
     so.mbl_product_tile_width.argtypes = [i32, i32, i32, i32]
     so.mbl_gap_ratio.restype = i32
     so.mbl_gap_ratio.argtypes = [i32, i32, p, i64, p, p, p]
+    so.mbl_entanglement_workspace_size.restype = i32
+    so.mbl_entanglement_workspace_size.argtypes = [pch, i32, i32, ctypes.POINTER(sz)]
+    so.mbl_entanglement_entropy.restype = i32
+    so.mbl_entanglement_entropy.argtypes = [pch, i32, i32, p, i64, p, p, sz, p]
     so.mbl_set_gram_engine.restype = i32
     so.mbl_set_gram_engine.argtypes = [i32]
     so.mbl_gram_workspace_size.restype = i32
@@ -420,3 +425,29 @@ def gap_ratio(evals, m=None):
                                ctypes.c_void_p(r_mean.data_ptr()), ctypes.c_void_p(count.data_ptr()),
                                _stream_ptr(evals)), "mbl_gap_ratio")
     return r_mean, count
+
+
+def entanglement_workspace_size(chain, l_a, nvec):
+    sz = ctypes.c_size_t(0)
+    _check(lib().mbl_entanglement_workspace_size(ctypes.byref(chain), int(l_a), int(nvec), ctypes.byref(sz)),
+           "mbl_entanglement_workspace_size")
+    return sz.value
+
+
+def entanglement_entropy(chain, l_a, V, workspace=None):
+    """mbl_entanglement_entropy of the columns of the n x nvec float64 CUDA tensor V (unit
+    column stride); returns a float64 CUDA tensor of nvec entropies."""
+    torch = _torch()
+    if V.dim() != 2 or V.dtype != torch.float64 or not V.is_cuda or V.stride(1) != 1:
+        raise ValueError("V: 2-D float64 CUDA tensor with unit column stride")
+    nvec = V.shape[1]
+    ldv = V.stride(0) if V.shape[0] > 1 else nvec
+    need = entanglement_workspace_size(chain, l_a, nvec)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=V.device)
+    S = torch.empty(nvec, dtype=torch.float64, device=V.device)
+    _check(lib().mbl_entanglement_entropy(ctypes.byref(chain), int(l_a), int(nvec), ctypes.c_void_p(V.data_ptr()),
+                                          int(ldv), ctypes.c_void_p(S.data_ptr()),
+                                          _dev(workspace, torch.uint8, "workspace"), workspace.numel(),
+                                          _stream_ptr(V)), "mbl_entanglement_entropy")
+    return S

@@ -56,4 +56,18 @@ template <typename T>
 int pcg_step(const ChainParams &cp, uint32_t n, int k, const T *dinv, T *r, T *p, T *t, T *w, const PcgDev &pd,
              cudaStream_t st);
 
+uint32_t host_binom(int n, int k);
+
+// Half-chain entanglement entropy (mbl_small.cu): per cut, the largest Gram side dmax,
+// the largest right-pattern count tmax, the largest block R x T (mmax), and the
+// workspace doubles of one (vector, p) block.
+struct EntanglementPlan {
+    int64_t dmax, tmax, mmax, block_doubles;
+    int blocks_per_vector;
+};
+EntanglementPlan entanglement_plan(int L, int n_up, int la);
+size_t entanglement_work_bytes(const EntanglementPlan &pl, int nvec);
+int entanglement_launch(int L, int n_up, int la, int nvec, const double *V, int64_t ldv, double *S, void *work,
+                        size_t work_bytes, cudaStream_t st);
+
 }  // namespace mbl

@@ -1,4 +1,6 @@
-// mbl_observables.cu -- localization indicators of converged eigenpairs (Sec. 2.2).
+// mbl_observables.cu -- localization indicators of converged eigenpairs (Sec. 2.2): the
+// ABI entries of the adjacent gap ratio (kernel below) and of the half-chain entanglement
+// entropy (kernels in mbl_small.cu, next to the Jacobi eigensolver they use).
 //
 // Adjacent gap ratio: one block per disorder realization.  The block loads the
 // realization's m levels into shared memory (padded to a power of two with +inf),
@@ -106,4 +108,42 @@ extern "C" int mbl_gap_ratio(int nprob, int m, const double *evals_dev, int64_t 
     k_gap_ratio<<<nprob, kGapThreads, (size_t)P * sizeof(double), (cudaStream_t)stream>>>(m, P, evals_dev, ld,
                                                                                            r_mean_dev, count_dev);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+// Largest Gram side the entanglement kernels accept (a one-block Jacobi per block).
+static constexpr int64_t kEntMaxSide = 512;
+
+static int ent_check(const mbl_chain *chain, int l_a, int nvec, mbl::EntanglementPlan *pl)
+{
+    if (!chain || nvec < 0) return MBL_ERR_ARG;
+    const int L = chain->L, m = chain->n_up;
+    if (L < 2 || L > 32 || m < 0 || m > L || l_a < 1 || l_a > L - 1) return MBL_ERR_ARG;
+    *pl = mbl::entanglement_plan(L, m, l_a);
+    if (pl->dmax > kEntMaxSide) return MBL_ERR_ARG;
+    return MBL_OK;
+}
+
+extern "C" int mbl_entanglement_workspace_size(const mbl_chain *chain, int l_a, int nvec, size_t *bytes)
+{
+    mbl::EntanglementPlan pl;
+    const int rc = ent_check(chain, l_a, nvec, &pl);
+    if (rc != MBL_OK) return rc;
+    if (!bytes) return MBL_ERR_ARG;
+    *bytes = mbl::entanglement_work_bytes(pl, nvec);
+    return MBL_OK;
+}
+
+extern "C" int mbl_entanglement_entropy(const mbl_chain *chain, int l_a, int nvec, const double *V_dev,
+                                        int64_t ldv, double *S_dev, void *workspace_dev, size_t workspace_bytes,
+                                        mbl_stream_t stream)
+{
+    mbl::EntanglementPlan pl;
+    const int rc = ent_check(chain, l_a, nvec, &pl);
+    if (rc != MBL_OK) return rc;
+    if (ldv < nvec) return MBL_ERR_ARG;
+    if (nvec == 0) return MBL_OK;
+    if (!V_dev || !S_dev || !workspace_dev) return MBL_ERR_ARG;
+    if (workspace_bytes < mbl::entanglement_work_bytes(pl, nvec)) return MBL_ERR_WORKSPACE;
+    return mbl::entanglement_launch(chain->L, chain->n_up, l_a, nvec, V_dev, ldv, S_dev, workspace_dev,
+                                    workspace_bytes, (cudaStream_t)stream);
 }

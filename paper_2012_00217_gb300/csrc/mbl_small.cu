@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "mbl_dense.h"
+#include "mbl_device.cuh"
 #include "mbl_internal.h"
 
 namespace mbl {
@@ -43,14 +44,16 @@ __host__ __device__ inline int pad_ld(int n) { return n | 1; }
 // with |a_pq| <= eps sqrt(|a_pp a_qq|) are skipped (the relative test keeps the small
 // eigenvalues of graded matrices accurate); sweeps stop when one rotates nothing or after
 // max_sweeps.  On exit diag(A) holds the eigenvalues and the columns of V (stride ld)
-// the eigenvectors.  Each warp rotates whole rows / columns of its pairs, lanes striding
-// the other index.  cs, pairs: n + 2 entries (shared memory).
-template <typename T>
+// the eigenvectors (WANT_V = false: eigenvalues only, V not touched).  Each warp rotates
+// whole rows / columns of its pairs, lanes striding the other index.  cs, pairs: n + 2
+// entries (shared or global memory of this block).
+template <typename T, bool WANT_V = true>
 __device__ void dev_jacobi(int n, int ld, T *A, T *V, T *cs, int *pairs, int *s_rot, int max_sweeps)
 {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-    for (int i = warp; i < n; i += nwarps)
-        for (int j = lane; j < n; j += 32) V[i * ld + j] = (i == j) ? (T)1 : (T)0;
+    if (WANT_V)
+        for (int i = warp; i < n; i += nwarps)
+            for (int j = lane; j < n; j += 32) V[i * ld + j] = (i == j) ? (T)1 : (T)0;
     __syncthreads();
     if (n < 2) return;
     const int np = (n + 1) & ~1;
@@ -109,13 +112,16 @@ __device__ void dev_jacobi(int n, int ld, T *A, T *V, T *cs, int *pairs, int *s_
                 const T c = cs[2 * i];
                 const int p = pairs[2 * i], q = pairs[2 * i + 1];
                 for (int j = lane; j < n; j += 32) {
-                    T *Aj = A + j * ld, *Vj = V + j * ld;
+                    T *Aj = A + j * ld;
                     const T ap = Aj[p], aq = Aj[q];
                     Aj[p] = c * ap - s * aq;
                     Aj[q] = s * ap + c * aq;
-                    const T vp = Vj[p], vq = Vj[q];
-                    Vj[p] = c * vp - s * vq;
-                    Vj[q] = s * vp + c * vq;
+                    if (WANT_V) {
+                        T *Vj = V + j * ld;
+                        const T vp = Vj[p], vq = Vj[q];
+                        Vj[p] = c * vp - s * vq;
+                        Vj[q] = s * vp + c * vq;
+                    }
                 }
             }
             __syncthreads();
@@ -629,5 +635,155 @@ int gather_cols(int k, int nev, const double *V, const int *sel, double *Csel, c
     k_gather_cols<<<1, 256, 0, st>>>(k, nev, V, sel, Csel);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------------
+// Half-chain entanglement entropy (Sec. 2.2) of sector vectors.  Cut after the first la
+// sites.  With p up spins on the left, a vector's entries form the R x T matrix
+// M_p[i][c] = v[off_c + i]: i the colex rank of the left pattern among those with p ones,
+// c the colex rank of the right pattern among those with n_up - p ones, off_c the row of
+// the first state with that right pattern (the left p spins lowest).  The reduced density
+// matrix of the left block is the direct sum of the M_p M_p^T.  One block per
+// (vector, p): M_p gathered densely into its workspace, the smaller Gram (M M^T or
+// M^T M, with the same nonzero eigenvalues), its eigenvalues by Jacobi (FP64), and the
+// sums s0 = sum lambda, s1 = sum lambda ln lambda over lambda > 0, in a fixed order.  A
+// second launch forms S = ln N - (sum_p s1) / N with N = sum_p s0 = ||v||^2, so v need
+// not be normalised.
+
+EntanglementPlan entanglement_plan(int L, int n_up, int la)
+{
+    EntanglementPlan pl{};
+    const int lb = L - la;
+    for (int p = 0; p <= la; ++p) {
+        const int q = n_up - p;
+        if (q < 0 || q > lb) continue;
+        const int64_t R = host_binom(la, p), T = host_binom(lb, q);
+        const int64_t d = R < T ? R : T;
+        if (d > pl.dmax) pl.dmax = d;
+        if (T > pl.tmax) pl.tmax = T;
+        if (R * T > pl.mmax) pl.mmax = R * T;
+    }
+    // M (mmax), A (dmax x pad_ld(dmax)), cs (dmax + 2), pairs and offsets (as doubles)
+    pl.block_doubles = pl.mmax + pl.dmax * (int64_t)pad_ld((int)pl.dmax) + 2 * (pl.dmax + 2) + pl.tmax + 8;
+    pl.blocks_per_vector = la + 1;
+    return pl;
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+    k_ent_block(int L, int n_up, int la, const double *__restrict__ V, int64_t ldv, double *work,
+                int64_t block_doubles, int64_t mmax, int64_t dmax, double *parts)
+{
+    __shared__ uint32_t sb[kBinomDim * kBinomDim];
+    __shared__ int s_rot;
+    __shared__ double s_r0[kSmallThreads / 32], s_r1[kSmallThreads / 32];
+    load_binom(sb);
+    __syncthreads();
+    const int e = blockIdx.x / (la + 1), p = blockIdx.x % (la + 1);
+    const int lb = L - la, q = n_up - p;
+    double *out = parts + 2 * (int64_t)blockIdx.x;
+    if (q < 0 || q > lb) {  // no state has p up spins on the left
+        if (threadIdx.x == 0) {
+            out[0] = 0.0;
+            out[1] = 0.0;
+        }
+        return;
+    }
+    const int R = (int)binom(sb, la, p), T = (int)binom(sb, lb, q);
+    const bool left = R <= T;  // Gram over the left patterns (d = R), else over the right ones
+    const int d = left ? R : T, ld = pad_ld(d);
+    double *M = work + (int64_t)blockIdx.x * block_doubles;  // R x T, row-major
+    double *A = M + mmax;
+    double *cs = A + dmax * (int64_t)pad_ld((int)dmax);
+    int *pairs = reinterpret_cast<int *>(cs + dmax + 2);
+    uint32_t *off = reinterpret_cast<uint32_t *>(cs + 2 * (dmax + 2));
+    for (int c = threadIdx.x; c < T; c += blockDim.x) {
+        const uint32_t b = cns_unrank(sb, lb, q, (uint32_t)c);
+        off[c] = cns_rank(sb, (b << la) | ((1u << p) - 1u));
+    }
+    __syncthreads();
+    const double *v = V + e;
+    for (int64_t x = threadIdx.x; x < (int64_t)R * T; x += blockDim.x) {
+        const int i = (int)(x % R), c = (int)(x / R);  // consecutive threads: consecutive rows of a tile
+        M[(int64_t)i * T + c] = v[((int64_t)off[c] + i) * ldv];
+    }
+    __syncthreads();
+    for (int64_t x = threadIdx.x; x < (int64_t)d * d; x += blockDim.x) {
+        const int i = (int)(x / d), j = (int)(x % d);
+        if (j < i) continue;
+        double acc = 0.0;
+        if (left) {
+            const double *mi = M + (int64_t)i * T, *mj = M + (int64_t)j * T;
+            for (int c = 0; c < T; ++c) acc += mi[c] * mj[c];
+        } else {
+            for (int r = 0; r < R; ++r) acc += M[(int64_t)r * T + i] * M[(int64_t)r * T + j];
+        }
+        A[(int64_t)i * ld + j] = acc;
+        A[(int64_t)j * ld + i] = acc;
+    }
+    __syncthreads();
+    dev_jacobi<double, false>(d, ld, A, nullptr, cs, pairs, &s_rot, kMaxSweeps);
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        const double lam = A[(int64_t)i * ld + i];
+        if (lam > 0.0) {
+            s0 += lam;
+            s1 += lam * log(lam);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_r0[threadIdx.x >> 5] = s0;
+        s_r1[threadIdx.x >> 5] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int w = 0; w < kSmallThreads / 32; ++w) {
+            a0 += s_r0[w];
+            a1 += s_r1[w];
+        }
+        out[0] = a0;
+        out[1] = a1;
+    }
+}
+
+__global__ void k_ent_combine(int nvec, int per, const double *parts, double *S)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nvec) return;
+    double n2 = 0.0, a1 = 0.0;
+    for (int p = 0; p < per; ++p) {
+        n2 += parts[2 * ((int64_t)e * per + p)];
+        a1 += parts[2 * ((int64_t)e * per + p) + 1];
+    }
+    S[e] = n2 > 0.0 ? log(n2) - a1 / n2 : NAN;
+}
+
+int entanglement_launch(int L, int n_up, int la, int nvec, const double *V, int64_t ldv, double *S, void *work,
+                        size_t work_bytes, cudaStream_t st)
+{
+    const EntanglementPlan pl = entanglement_plan(L, n_up, la);
+    const int64_t nblk = (int64_t)nvec * pl.blocks_per_vector;
+    const size_t need = entanglement_work_bytes(pl, nvec);
+    if (work_bytes < need) return MBL_ERR_WORKSPACE;
+    double *w = (double *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    double *parts = w + nblk * pl.block_doubles;
+    note_launch();
+    k_ent_block<<<(unsigned)nblk, kSmallThreads, 0, st>>>(L, n_up, la, V, ldv, w, pl.block_doubles, pl.mmax,
+                                                          pl.dmax, parts);
+    if (cudaGetLastError() != cudaSuccess) return MBL_ERR_CUDA;
+    note_launch();
+    k_ent_combine<<<(nvec + 127) / 128, 128, 0, st>>>(nvec, pl.blocks_per_vector, parts, S);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+size_t entanglement_work_bytes(const EntanglementPlan &pl, int nvec)
+{
+    const int64_t nblk = (int64_t)nvec * pl.blocks_per_vector;
+    return (size_t)(nblk * pl.block_doubles + 2 * nblk + 64) * sizeof(double) + 256;
+}
+
 
 }  // namespace mbl

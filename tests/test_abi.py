@@ -247,6 +247,34 @@ def test_gap_ratio_checks_arguments_before_any_launch(so):
         assert so.mbl_gap_ratio(nprob, m, ptrs[0], ld, ptrs[1], ptrs[2], None) == want
 
 
+def test_entanglement_workspace_and_argument_checks(so):
+    import paper_2012_00217_gb300 as mbl
+    from paper_2012_00217_gb300 import binding
+    bad = binding.MBL_ERR_ARG
+    ch = mbl.make_chain(20, np.zeros(20))
+    prev = 0
+    for nvec in (1, 4, 16):
+        b = binding.entanglement_workspace_size(ch, 10, nvec)
+        assert b > prev
+        prev = b
+    # the half cut at L = 20: 11 blocks of (252 x 252 gather, 252 x 253 Gram) per column
+    assert 11 * 16 * 8 * 2 * 252 * 252 < binding.entanglement_workspace_size(ch, 10, 16) < 2 ** 28
+    sz = ctypes.c_size_t(0)
+    for L, n_up, l_a, nvec in ((20, 10, 0, 1), (20, 10, 20, 1), (20, 10, 5, -1), (24, 12, 12, 1), (33, 16, 8, 1)):
+        h = np.zeros(max(L, 1))
+        c = binding.Chain(L, n_up, 0, 1.0, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert so.mbl_entanglement_workspace_size(ctypes.byref(c), l_a, nvec, ctypes.byref(sz)) == bad
+    # a cut whose Gram sides stay small is fine at L = 24 (one site on the left)
+    c24 = mbl.make_chain(24, np.zeros(24))
+    assert binding.entanglement_workspace_size(c24, 1, 2) > 0
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every case below fails its checks or launches nothing
+    assert so.mbl_entanglement_entropy(ctypes.byref(ch), 10, 4, fake, 3, fake, fake, 1 << 30, None) == bad
+    assert so.mbl_entanglement_entropy(ctypes.byref(ch), 10, 4, None, 4, fake, fake, 1 << 30, None) == bad
+    assert so.mbl_entanglement_entropy(ctypes.byref(ch), 10, 4, fake, 4, fake, fake, 16,
+                                       None) == binding.MBL_ERR_WORKSPACE
+    assert so.mbl_entanglement_entropy(ctypes.byref(ch), 10, 0, None, 0, None, None, 0, None) == binding.MBL_OK
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2012_00217_gb300 import binding
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "absent.so"))

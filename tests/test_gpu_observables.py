@@ -79,3 +79,53 @@ def test_empty_batch_is_a_no_op(mbl):
     E = torch.empty((0, 8), dtype=torch.float64, device=DEV)
     r, c = mbl.gap_ratio(E)
     assert r.numel() == 0 and c.numel() == 0
+
+
+# ---------------------------------------------------------------- entanglement entropy
+@pytest.mark.parametrize("L,n_up,l_a", [(8, 4, 4), (10, 5, 5), (10, 5, 1), (10, 5, 9), (11, 4, 6), (12, 6, 6),
+                                        (14, 7, 7), (16, 8, 8), (13, 6, 3)])
+def test_entropy_random_vectors(mbl, L, n_up, l_a):
+    rng = np.random.default_rng(L * 100 + l_a)
+    st = ham.basis(L, n_up)
+    V = rng.normal(size=(st.size, 5)) * np.array([1.0, 2.5, 1e-3, 1.0, 7.0])
+    V[:, 3] = 0.0
+    V[7 % st.size, 3] = 1.0  # a basis state: S = 0
+    chain = mbl.make_chain(L, np.zeros(L), 1.0, False, n_up)
+    S = mbl.entanglement_entropy(chain, l_a, torch.from_numpy(V).to(DEV)).cpu().numpy()
+    for e in range(V.shape[1]):
+        want = obs.entanglement_entropy(st, V[:, e], l_a)
+        assert abs(S[e] - want) <= 1e-10, (e, S[e], want)
+
+
+def test_entropy_of_eigenvectors_and_strided_input(mbl):
+    # eigenvectors of the L = 12 chain at weak and strong disorder (dense), read from a
+    # wider row-major block (ld > nvec); a zero column gives NaN
+    L = 12
+    st = ham.basis(L, 6)
+    cols = []
+    for W in (0.5, 8.0):
+        h = wl.fields(L, W, 3)
+        ev, Vd = np.linalg.eigh(ham.dense_sector(ham.Chain(L, h)))
+        cols += [Vd[:, 400], Vd[:, 462]]
+    V = np.zeros((st.size, 8))
+    V[:, :4] = np.array(cols).T
+    Vg = torch.from_numpy(V).to(DEV)[:, :5]  # ld = 8, nvec = 5; column 4 is zero
+    chain = mbl.make_chain(L, np.zeros(L))
+    S = mbl.entanglement_entropy(chain, 6, Vg).cpu().numpy()
+    for e in range(4):
+        assert abs(S[e] - obs.entanglement_entropy(st, cols[e], 6)) <= 1e-10
+    assert math.isnan(S[4])
+    # volume-law vs area-law: weak-disorder eigenstates are far more entangled
+    assert min(S[0], S[1]) > max(S[2], S[3])
+
+
+def test_entropy_half_cut_l20_sampled(mbl):
+    # the bench size (L = 20, half cut: Gram blocks up to 252 x 252), two random columns
+    L = 20
+    st = ham.basis(L, 10)
+    rng = np.random.default_rng(20)
+    V = rng.normal(size=(st.size, 2))
+    chain = mbl.make_chain(L, np.zeros(L))
+    S = mbl.entanglement_entropy(chain, 10, torch.from_numpy(V).to(DEV)).cpu().numpy()
+    for e in range(2):
+        assert abs(S[e] - obs.entanglement_entropy(st, V[:, e], 10)) <= 1e-9
