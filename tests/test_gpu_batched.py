@@ -59,3 +59,34 @@ def test_batched_matches_dense(mbl, given_sigma):
             e1, _, _, _ = mbl.lobpcg_solve(chains[i], sig[i], o1, X0[off:off + n].contiguous(), w1)
             assert np.array_equal(e1, evals[i])
             off += n
+
+
+def test_several_windows_and_sectors_per_realization(mbl):
+    """Several spectral windows of one realization, and sectors other than S^z = 0, in one
+    batched call: each (realization, sector, sigma) problem must give the dense-LAPACK
+    eigenvalues of its sector nearest its own sigma, and the gap ratio of each window (on
+    the GPU) must equal the oracle's on the same levels."""
+    from oracle import observables as obs
+    L, nev, k = 12, 6, 12
+    h = wl.batched_fields(L, 3.0, 11)
+    probs = []
+    for n_up in (6, 5, 4):
+        ev = np.linalg.eigvalsh(ham.dense_sector(ham.Chain(L, h, n_up=n_up)))
+        for q in (0.2, 0.5, 0.8):  # three windows across the sector's spectrum
+            probs.append(dict(n_up=n_up, ev=ev, sigma=float(np.quantile(ev, q))))
+    chains = [mbl.make_chain(L, h, 1.0, False, p["n_up"]) for p in probs]
+    X0 = torch.cat([torch.from_numpy(wl.initial_block(p["ev"].size, k, 40 + i)) for i, p in enumerate(probs)])
+    nh = max(max(abs(p["ev"][0]), abs(p["ev"][-1])) for p in probs)
+    opts = mbl.make_opts(nev, k, tol=1e-8, max_iter=1000, pcg_iters=80, norm_h=nh, mode=mbl.MODE_MIXED)
+    ws = torch.empty(mbl.binding.batched_workspace_size(chains, opts, 4), dtype=torch.uint8, device=DEV)
+    evals, resid, stats, rc = mbl.binding.lobpcg_solve_batched(chains, opts, X0.to(DEV), ws, 4,
+                                                               sigmas=[p["sigma"] for p in probs])
+    for i, p in enumerate(probs):
+        assert stats[i]["converged"] == 1
+        want = np.sort(p["ev"][np.lexsort((p["ev"], np.abs(p["ev"] - p["sigma"])))[:nev]])
+        assert np.abs(evals[i] - want).max() <= 1e-9 * nh, (i, evals[i], want)
+    r, c = mbl.gap_ratio(torch.from_numpy(np.ascontiguousarray(evals)).to(DEV))
+    r, c = r.cpu().numpy(), c.cpu().numpy()
+    for i in range(len(probs)):
+        want, n = obs.gap_ratio_mean(evals[i])
+        assert c[i] == n and abs(r[i] - want) <= 1e-13
