@@ -236,6 +236,28 @@ def test_autotune_checks_arguments_before_any_launch(so):
         assert rc == binding.MBL_ERR_ARG  # the last case: X and Y overlap
 
 
+def test_non_finite_chain_or_shift_is_refused_on_the_host(so):
+    """Host-side fault injection: NaN or Inf in a field, in delta or in sigma is an
+    argument error, found before any device work (the pointers below are never used)."""
+    import paper_2012_00217_gb300 as mbl
+    from paper_2012_00217_gb300 import binding
+    bad = binding.MBL_ERR_ARG
+    n = math.comb(12, 6)
+    fake = ctypes.c_void_p(1 << 20)
+    for field, delta, sigma in ((np.nan, 1.0, 0.0), (np.inf, 1.0, 0.0), (0.5, np.nan, 0.0), (0.5, 1.0, np.inf)):
+        h = np.zeros(12)
+        h[3] = field
+        ch = mbl.make_chain(12, h, delta)
+        assert so.mbl_hamiltonian_apply(ctypes.byref(ch), ctypes.c_double(sigma), 1, fake, 8, fake, 8, n, 8,
+                                        None) == bad
+        opts = mbl.make_opts(4, 8)
+        ev, res = np.zeros(4), np.zeros(4)
+        st = binding.LobpcgStats()
+        assert so.mbl_lobpcg_solve(ctypes.byref(ch), ctypes.c_double(sigma), ctypes.byref(opts), fake, fake,
+                                   ctypes.c_size_t(1 << 40), ev.ctypes.data_as(ctypes.c_void_p), None,
+                                   res.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st), None) == bad
+
+
 def test_gap_ratio_checks_arguments_before_any_launch(so):
     from paper_2012_00217_gb300 import binding
     ok, bad = binding.MBL_OK, binding.MBL_ERR_ARG
