@@ -240,21 +240,28 @@ int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts
                      double *evals_host, double *evecs_dev, double *resid_host,
                      mbl_lobpcg_stats *stats, mbl_stream_t stream);
 
-/* Same solve for callers that cannot allocate device memory: code running while a
- * stream is being captured into a CUDA graph (where an allocation would be recorded into
- * the graph or fail), plug-ins whose host application's own allocator owns the device
- * memory pool, and real-time callers with a fixed memory budget decided up front.  The
- * paper has no counterpart; this entry point only changes where the workspace lives.
+/* Same solve for callers that cannot allocate device memory when they need a solve:
+ * plug-ins whose host application's own allocator owns the whole device memory pool,
+ * and real-time callers whose memory budget is fixed up front.  The paper has no
+ * counterpart; this entry point only changes where the workspace lives.
  * The workspace is one fixed device array of MBL_NOALLOC_SCRATCH_BYTES (16 MiB) inside
  * the library, present on every GPU that loads the library until the process exits;
  * problems whose mbl_lobpcg_workspace_size exceeds it are rejected with
  * MBL_ERR_WORKSPACE before anything is launched (16 MiB covers, for instance, L = 12 with
- * k <= 64, L = 14 with k <= 32 and L = 16 with k = 8).  The call allocates nothing: no cudaMalloc or cudaFree,
- * no graph instantiation (opts->use_graph is ignored) and no timing events
- * (opts->timing is ignored).  The first call on a device looks up the array's device
- * address with that device current.  Every call shares the one array and leaves its
- * contents behind; the solver clears what must start at zero.  Calls whose work overlaps
- * on the GPU (other streams, other host threads) race on the array: serialise them.
+ * k <= 64, L = 14 with k <= 32 and L = 16 with k = 8).  The call allocates nothing: no
+ * cudaMalloc or cudaFree, no graph instantiation (opts->use_graph is ignored) and no
+ * timing events (opts->timing is ignored).
+ * Set-up: the first call on a device looks up the array's device address with that
+ * device current; with lazy module loading the module (and its 16 MiB) is loaded at the
+ * library's first use on that device, so make one call of this library on each device
+ * (this one, or any other) before the caller's memory budget is fixed.
+ * The stream must belong to the current device (else MBL_ERR_ARG).  Like
+ * mbl_lobpcg_solve, the call synchronises the stream at set-up and once per iteration
+ * and writes host results, so it cannot be issued on a stream that is being captured
+ * into a CUDA graph.
+ * Every call shares the one array and leaves its contents behind; the solver clears
+ * what must start at zero.  Calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on the array: serialise them.
  * Arguments and results are those of mbl_lobpcg_solve. */
 #define MBL_NOALLOC_SCRATCH_BYTES (16u << 20)
 int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
@@ -269,8 +276,9 @@ int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, const mbl_lob
  * overlap on the GPU.  The workers start after the work already queued on `stream`, and
  * the call returns when every problem has finished.
  *   sigmas:   nprob shifts, or NULL: sigma_i = (E_min + E_max)/2 of problem i from
- *             LOBPCG bounds on +-H (block 4, tolerance 1e-7, started from the first four
- *             columns of its X0 block); then, if opts->norm_h <= 0, ||H|| = max |E|.
+ *             the Lanczos bounds of mbl_spectrum_bounds (tolerance 1e-7, at most 1000
+ *             steps, started from column 0 of its X0 block); then, if opts->norm_h <= 0,
+ *             ||H|| = max |E|.
  *   X0_dev:   the problems' n_i x k FP64 start blocks packed one after another.
  *   workspace: mbl_batched_workspace_size bytes (nstreams slots of the largest problem).
  *   evals_host, resid_host: nprob x nev (problem-major); evecs_dev: the n_i x nev blocks

@@ -680,6 +680,11 @@ extern "C" int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, co
     int rc = mbl_lobpcg_workspace_size(chain, opts, &need);
     if (rc != MBL_OK) return rc;
     if (need > kNoAllocBytes) return MBL_ERR_WORKSPACE;
+    // the array looked up below is the current device's: the stream must run there
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess)
+        return MBL_ERR_CUDA;
+    if (sdev != cur) return MBL_ERR_ARG;
     void *ws = nullptr;
     rc = noalloc_scratch(&ws);
     if (rc != MBL_OK) return rc;

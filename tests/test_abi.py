@@ -50,6 +50,16 @@ def test_binding_covers_the_header(so):
     assert sorted(binding.EXPORTED) == _declared()
 
 
+def test_noalloc_entry_point_and_its_limit(so):
+    """The allocation-free solve is exported, and the binding's copy of its scratch size
+    equals the header's MBL_NOALLOC_SCRATCH_BYTES (the refusal test relies on it)."""
+    from paper_2012_00217_gb300 import binding
+    assert hasattr(so, "mbl_lobpcg_solve_noalloc")
+    m = re.search(r"#define\s+MBL_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", open(HEADER).read())
+    assert m, "MBL_NOALLOC_SCRATCH_BYTES not found in the header"
+    assert binding.NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+
+
 def _c_layout(tmp_path):
     gcc = shutil.which("gcc")
     if gcc is None:
