@@ -180,6 +180,32 @@ def dense_sector(chain):
     return apply(chain, 0.0, np.eye(n))
 
 
+def sparse_sector(chain):
+    """The sector block of H as a scipy CSR matrix, from the matrix elements of
+    Eq. (Hmatrix) entry by entry: d(s) on the diagonal, and for every bond (i, j) and
+    every state s whose spins i and j differ, 1/2 at (rank(s'), rank(s)) with s' = s
+    with those two spins exchanged (ranks by bisection in the enumerated basis).
+    For the shift-invert Lanczos reference at sizes where the dense matrix does not fit."""
+    import scipy.sparse as sp
+    st = basis(chain.L, chain.n_up)
+    n = st.size
+    L = chain.L
+    bonds = [(i, i + 1) for i in range(L - 1)]
+    if chain.periodic and L > 2:
+        bonds.append((L - 1, 0))
+    rows, cols, vals = [np.arange(n)], [np.arange(n)], [diag(chain)]
+    for (i, j) in bonds:
+        differ = ((st >> np.uint32(i)) ^ (st >> np.uint32(j))) & np.uint32(1)
+        src = np.nonzero(differ)[0]
+        dst = rank(st, st[src] ^ np.uint32((1 << i) | (1 << j)))
+        if np.any(dst < 0):
+            raise RuntimeError("an exchanged state left the sector")
+        rows.append(dst)
+        cols.append(src)
+        vals.append(np.full(src.size, 0.5))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
 # Pauli matrices written in the single-site basis (index 0 = bit 0 = spin down,
 # index 1 = bit 1 = spin up), so that Z|up> = +|up>, X|up> = |down> and
 # Y|up> = i|down>, Y|down> = -i|up>.

@@ -35,6 +35,29 @@ def test_sector_block_equals_pauli_build(L, periodic, delta):
         assert np.array_equal(got, ref) or np.abs(got - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("L", [4, 6, 8, 10])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_sparse_sector_equals_pauli_build(L, periodic):
+    """The entry-by-entry sparse sector matrix (used by the shift-invert references) is
+    the Pauli-Kronecker matrix of Eq. (Hmatrix) restricted to each sector."""
+    pytest.importorskip("scipy.sparse")
+    ch = _chain(L, periodic, 0.8, seed=20 + L)
+    full = ham.dense_full_pauli(ch).real
+    for n_up in range(L + 1):
+        ch.n_up = n_up
+        st = ham.basis(L, n_up).astype(np.int64)
+        got = ham.sparse_sector(ch).toarray()
+        assert np.abs(got - full[np.ix_(st, st)]).max() <= 1e-14 * max(1.0, np.abs(full).max())
+
+
+def test_sparse_sector_product_matches_c_product_l16():
+    pytest.importorskip("scipy.sparse")
+    ch = _chain(16, True, 1.0, W=8.0, seed=5)
+    X = wl.block(ham.sector_dim(16, 8), 3, 7)
+    d = ham.sparse_sector(ch) @ X - ham.apply(ch, 0.0, X)
+    assert np.abs(d).max() <= 1e-12 * np.abs(X).max()
+
+
 @pytest.mark.parametrize("periodic", [False, True])
 def test_full_hamiltonian_conserves_total_sz(periodic):
     L = 8
