@@ -118,6 +118,28 @@ __device__ __forceinline__ void stv(T *p, const Vec<T, V> &x)
     *reinterpret_cast<Vec<T, V> *>(p) = x;
 }
 
+// Load with the streaming (evict-first) hint: for rows that will not be read again while
+// they could still be in L2 (high-bond partners more than kFarBytes away in the vector).
+template <typename T, int V>
+__device__ __forceinline__ Vec<T, V> ldv_stream(const T *p)
+{
+    if constexpr ((V * sizeof(T)) % 16 == 0) {
+        Vec<T, V> x;
+        const float4 *src = reinterpret_cast<const float4 *>(p);
+        float4 *dst = reinterpret_cast<float4 *>(&x);
+#pragma unroll
+        for (int i = 0; i < (int)(V * sizeof(T) / 16); ++i) dst[i] = __ldcs(src + i);
+        return x;
+    } else {
+        return ldv<T, V>(p);
+    }
+}
+
+#ifndef MBL_FAR_BYTES
+#define MBL_FAR_BYTES (48ll << 20)
+#endif
+constexpr long long kFarBytes = MBL_FAR_BYTES;
+
 // Store with the evict-first hint: a product's output is not read again by the same
 // launch, so it should not push the input's rows out of L2.
 template <typename T, int V>
@@ -285,7 +307,21 @@ __device__ __forceinline__ void finish_column_sums(const Reduce &rd, int k, doub
     const int c = threadIdx.x / per, j = threadIdx.x % per;
     double acc = 0.0;
     if (c < k) {
-        for (int b = j; b < (int)gridDim.x; b += per) acc += rd.partials[(int64_t)b * k + c];
+        // blocks j, j + per, ... in that order, eight requested at a time
+        constexpr int kBatch = 8;
+        for (int b0 = j; b0 < (int)gridDim.x; b0 += kBatch * per) {
+            double q[kBatch];
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+                const int b = b0 + i * per;
+                q[i] = b < (int)gridDim.x ? rd.partials[(int64_t)b * k + c] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+                if (b0 + i * per >= (int)gridDim.x) break;
+                acc += q[i];
+            }
+        }
     }
     s_tree[threadIdx.x] = acc;
     __syncthreads();
@@ -348,13 +384,25 @@ __device__ __forceinline__ void finish_column_sums_f32(const Reduce &rd, int k, 
     const int c = threadIdx.x / per, j = threadIdx.x % per;
     float sum = 0.0f, cmp = 0.0f;
     if (c < k) {
+        // the partials of blocks j, j + per, j + 2 per, ... in that order, requested eight at
+        // a time so that the serial tail waits for few memory round trips
         const float2 *pp = reinterpret_cast<const float2 *>(rd.partials);
-        for (int b = j; b < (int)gridDim.x; b += per) {
-            const float2 q = pp[(int64_t)b * k + c];
-            float hi, e;
-            two_sum(sum, q.x, hi, e);
-            sum = hi;
-            cmp += e + q.y;
+        constexpr int kBatch = 8;
+        for (int b0 = j; b0 < (int)gridDim.x; b0 += kBatch * per) {
+            float2 q[kBatch];
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+                const int b = b0 + i * per;
+                q[i] = b < (int)gridDim.x ? pp[(int64_t)b * k + c] : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+                if (b0 + i * per >= (int)gridDim.x) break;
+                float hi, e;
+                two_sum(sum, q[i].x, hi, e);
+                sum = hi;
+                cmp += e + q[i].y;
+            }
         }
     }
     s_tree2[threadIdx.x] = make_float2(sum, cmp);
@@ -560,6 +608,15 @@ __host__ __device__ inline int lowtab_base(int B) { return (1 << B) - 4; }
 #ifndef MBL_TILED_MIN_BLOCKS
 #define MBL_TILED_MIN_BLOCKS 3
 #endif
+// Bytes per lane of rows from the rest of the vector requested before a row's in-tile work
+#ifndef MBL_ROW_EARLY_BYTES
+#define MBL_ROW_EARLY_BYTES 64
+#endif
+// 1: the PCG solution update w += alpha p runs in the direction-update launch (a streaming
+// kernel), 0: in the epilogue of the q-launch
+#ifndef MBL_PCG_W_IN_UPDATE
+#define MBL_PCG_W_IN_UPDATE 1
+#endif
 
 // Per-tile values of a tile t (p = n_up - popc(t) up spins in its low part), computed
 // by one warp, one lane each: the tile's first row (lane 0), the diagonal constant of
@@ -607,13 +664,57 @@ __device__ __forceinline__ void tile_meta_warp(const uint32_t *sbin, const T *ta
     if (lane == 31) tm.offper = v32;
 }
 
-// One pass of a warp over RPW rows of a tile (row j of this lane group, `valid` when
-// j < tile size).  Own row and in-tile neighbours come from Xt (row stride ldt: the
+// Packed FP32 pair arithmetic (FADD2 / FMUL2 / FFMA2 on sm_100 and later): each is two
+// independent, correctly rounded operations, so the results equal those of the scalar
+// instructions bit for bit; the FP64 kernels use the scalar forms.
+template <typename T, int V>
+__device__ __forceinline__ void vadd(T (&s)[V], const Vec<T, V> &a)
+{
+    if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            const float2 r = __fadd2_rn(make_float2(s[v], s[v + 1]), make_float2(a.v[v], a.v[v + 1]));
+            s[v] = r.x;
+            s[v + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) s[v] += a.v[v];
+    }
+}
+
+// acc = 1/2 nb + (d x), with d x rounded on its own (exact 1/2: one rounding for the fma).
+template <typename T, int V>
+__device__ __forceinline__ void half_sum_plus_dx(T (&acc)[V], const T (&nb)[V], T d, const Vec<T, V> &x)
+{
+    if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+        const float2 d2 = make_float2(d, d), h2 = make_float2(0.5f, 0.5f);
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            const float2 dx = __fmul2_rn(d2, make_float2(x.v[v], x.v[v + 1]));
+            const float2 r = __ffma2_rn(h2, make_float2(nb[v], nb[v + 1]), dx);
+            acc[v] = r.x;
+            acc[v + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fma_rn((T)0.5, nb[v], mul_rn(d, x.v[v]));
+    }
+}
+
+// One pass of a warp over RPW rows of a tile (row j of this lane group, `valid` when it
+// is a row of the work item; otherwise j is some other row of the same tile and only the
+// output is dropped).  Own row and in-tile neighbours come from Xt (row stride ldt: the
 // tile in shared memory, or X itself from the tile's first row); the joining, wrap and
 // high-bond rows from X.  y = (d - sigma) x + 1/2 (sum of neighbour rows), the
-// neighbours summed first in a fixed order (joining, wrap, low bonds, high bonds):
+// neighbours summed first in a fixed order (low bonds, joining, wrap, high bonds):
 // scaling by 1/2 is exact, so only the order of the additions is a choice, and every
-// variant (persistent, ordered, staged) makes the same one.
+// work order (persistent, ordered, staged, streamed) makes the same one.  The rows from
+// the rest of the vector (joining and wrap partners, the first high-bond rows) are
+// requested before the in-tile work so that their latency overlaps it.  Every load reads
+// a row of the chain's vector (the own row where a bond does not apply, row 0 of the
+// tile in an unused low-bond slot, the last shift past a tile's high bonds); only the
+// additions are conditional, so no register has to be cleared before a load.
 template <typename T, int V, int NB, int MODE>
 __device__ __forceinline__ void tile_row_pass(const ChainParams &cp, int B, const T *__restrict__ X, int64_t ldx,
                                               const T *__restrict__ Xt, int64_t ldt, const LowRec *__restrict__ rp,
@@ -623,93 +724,109 @@ __device__ __forceinline__ void tile_row_pass(const ChainParams &cp, int B, cons
                                               const T *__restrict__ dinv, const T *s_alpha, T (&part)[V],
                                               void *ps_w, const void *ps_p)
 {
+    constexpr int kVecBytes = V * (int)sizeof(T);
+    // early global rows: joining + wrap + kEarly high-bond rows, MBL_ROW_EARLY_BYTES per lane
+    constexpr int kEarly = MBL_ROW_EARLY_BYTES / kVecBytes - 2 > 0 ? MBL_ROW_EARLY_BYTES / kVecBytes - 2 : 0;
+    // in-tile rows requested together (64 bytes per lane)
+    constexpr int NBL = 64 / kVecBytes > 1 ? 64 / kVecBytes : 1;
     const uint32_t r = tm.off + j;
     const T *__restrict__ xr = X + (int64_t)r * ldx + col;
-    uint4 w0 = make_uint4(0, 0, 0, 0), w1 = make_uint4(0, 0, 0, 0);
-    if (valid) {
-        w0 = __ldg(reinterpret_cast<const uint4 *>(rp + j));
-        w1 = __ldg(reinterpret_cast<const uint4 *>(rp + j) + 1);
-    }
+    const uint4 w0 = __ldg(reinterpret_cast<const uint4 *>(rp + j));
+    const uint4 w1 = __ldg(reinterpret_cast<const uint4 *>(rp + j) + 1);
     const uint32_t u = w0.x & 0xffffu, cnt = (w0.x >> 16) & 0xffu, alow = w0.x >> 24;
     const uint32_t ub = (u >> (B - 1)) & 1u;
-    const bool join = valid && ub != t0;
-    const bool wrap = valid && cp.periodic && (u & 1u) != thi;
+    const bool join = ub != t0;
+    const bool wrap = cp.periodic && (u & 1u) != thi;
+    const int nh = tm.nh;
+    // the joining and wrap partners apply to about half of the rows each: loaded only there
+    Vec<T, V> ja, wb;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        ja.v[v] = (T)0;
+        wb.v[v] = (T)0;
+    }
+    if (join) ja = ldv<T, V>(xr + (ub ? (int64_t)sup : -(int64_t)sdn) * ldx);
+    if (wrap) wb = ldv<T, V>(X + (int64_t)(tm.offper + (w0.y & 0xffffu)) * ldx + col);
+    // the q-launch's own rows of r and M^-1, needed after the sum
+    Vec<T, V> rq;
+    T dq = (T)0;
+    if constexpr (MODE == kPcgQ) {
+        rq = ldv<T, V>(R + (int64_t)r * ldy + col);
+        dq = dinv[r];
+    }
+    Vec<T, V> hb[kEarly > 0 ? kEarly : 1];
+#pragma unroll
+    for (int e = 0; e < kEarly; ++e) {
+        const int hh = e < nh ? e : (nh > 0 ? nh - 1 : 0);
+        hb[e] = ldv<T, V>(nh > 0 ? xr + (int64_t)(int32_t)tm.shift[hh] * ldx : xr);
+    }
     T nb[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) nb[v] = (T)0;
     {
-        // (every conditionally loaded vector starts at zero: adding +0 is exact, and
-        // values left undefined on some lanes make the register allocator spill)
-        Vec<T, V> ja, wb;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            ja.v[v] = (T)0;
-            wb.v[v] = (T)0;
-        }
-        if (join) ja = ldv<T, V>(xr + (ub ? (int64_t)sup : -(int64_t)sdn) * ldx);
-        if (wrap) wb = ldv<T, V>(X + (int64_t)(tm.offper + (w0.y & 0xffffu)) * ldx + col);
-#pragma unroll
-        for (int v = 0; v < V; ++v) nb[v] += ja.v[v];
-        if (cp.periodic) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) nb[v] += wb.v[v];
-        }
-    }
-    {
-        // in-tile neighbours; the loop runs to the warp's largest count (no arithmetic
-        // past it: FP64 is ALU-bound here)
+        // in-tile neighbours; the loop runs to the warp's largest count
         const uint32_t nbw[6] = {w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
         const int cmax = (int)__reduce_max_sync(0xffffffffu, valid ? cnt : 0u);
 #pragma unroll
-        for (int q0 = 0; q0 < 12; q0 += NB) {
+        for (int q0 = 0; q0 < 12; q0 += NBL) {
             if (q0 >= cmax) break;
-            Vec<T, V> a[NB];
+            Vec<T, V> a[NBL];
 #pragma unroll
-            for (int e = 0; e < NB; ++e) {
+            for (int e = 0; e < NBL; ++e) {
                 const int q = q0 + e;
-                const int qq = q < 12 ? q : 11;  // slots past 12 are never loaded
+                const int qq = q < 12 ? q : 11;
                 const uint32_t jn = (nbw[qq >> 1] >> (16 * (qq & 1))) & 0xffffu;
-#pragma unroll
-                for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
-                if (q < (int)cnt) a[e] = ldv<T, V>(Xt + (int64_t)jn * ldt + col);
+                a[e] = ldv<T, V>(Xt + (int64_t)jn * ldt + col);
             }
 #pragma unroll
-            for (int e = 0; e < NB; ++e)
-                if (q0 + e < cmax) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) nb[v] += a[e].v[v];
-                }
+            for (int e = 0; e < NBL; ++e)
+                if (q0 + e < (int)cnt) vadd<T, V>(nb, a[e]);
         }
     }
-    for (int h0 = 0; h0 < tm.nh; h0 += NB) {
-        // high-bond neighbours: the tile's rows moved as a block, one shift per bond
+    if (join) vadd<T, V>(nb, ja);
+    if (wrap) vadd<T, V>(nb, wb);
+#pragma unroll
+    for (int e = 0; e < kEarly; ++e)
+        if (e < nh) vadd<T, V>(nb, hb[e]);
+    for (int h0 = kEarly; h0 < nh; h0 += NB) {
+        // the remaining high-bond neighbours: the tile's rows moved as a block, one shift
+        // per bond
         Vec<T, V> a[NB];
 #pragma unroll
         for (int e = 0; e < NB; ++e) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) a[e].v[v] = (T)0;
-            if (valid && h0 + e < tm.nh) a[e] = ldv<T, V>(xr + (int64_t)(int32_t)tm.shift[h0 + e] * ldx);
+            const int hh = h0 + e < nh ? h0 + e : nh - 1;
+            const int64_t sh = (int64_t)(int32_t)tm.shift[hh] * ldx;
+            // the shift is the same for the whole tile: a uniform choice of hint
+            if ((sh < 0 ? -sh : sh) * (int64_t)sizeof(T) >= kFarBytes)
+                a[e] = ldv_stream<T, V>(xr + sh);
+            else
+                a[e] = ldv<T, V>(xr + sh);
         }
 #pragma unroll
         for (int e = 0; e < NB; ++e)
-            if (h0 + e < tm.nh) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) nb[v] += a[e].v[v];
-            }
+            if (h0 + e < nh) vadd<T, V>(nb, a[e]);
     }
-    Vec<T, V> x;
-#pragma unroll
-    for (int v = 0; v < V; ++v) x.v[v] = (T)0;
-    if (valid) x = ldv<T, V>(Xt + (int64_t)j * ldt + col);
+    const Vec<T, V> x = ldv<T, V>(Xt + (int64_t)j * ldt + col);
     const T d = (tm.ct + (tab[u & 255u] + tab[256 + (u >> 8)])) -
                 mul_rn(hdelta, (T)(alow + (join ? 1u : 0u) + (wrap ? 1u : 0u)));
     T acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = fma_rn((T)0.5, nb[v], mul_rn(d, x.v[v]));
+    half_sum_plus_dx<T, V>(acc, nb, d, x);
     if (valid) {
         T alpha[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) alpha[v] = (MODE == kPcgQ) ? s_alpha[col + v] : (T)0;
+        if constexpr (MODE == kPcgQ) {
+            if (ps_w == nullptr) {
+                // r -= alpha q and r.(M^-1 r) on the prefetched row (as finish_row does)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    rq.v[v] -= alpha[v] * acc[v];
+                    part[v] += rq.v[v] * (dq * rq.v[v]);
+                }
+                stv<T, V>(R + (int64_t)r * ldy + col, rq);
+                return;
+            }
+        }
         finish_row<T, V, MODE>(acc, 0, r, Y, ldy, R, dinv, col, alpha, part, (T *)ps_w, (const T *)ps_p);
     }
 }
@@ -797,7 +914,8 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS) k_apply_tiled(
         const T *__restrict__ Xt = X + (int64_t)tm.off * ldx;
         for (uint32_t j0 = j_begin; j0 < j_end; j0 += RPW) {
             const uint32_t j = j0 + grp;
-            tile_row_pass<T, V, NB, MODE>(cp, B, X, ldx, Xt, ldx, rp, j, j < j_end, tm, tab, hdelta, t0, thi, sup,
+            tile_row_pass<T, V, NB, MODE>(cp, B, X, ldx, Xt, ldx, rp, min(j, j_end - 1u), j < j_end, tm, tab, hdelta,
+                                          t0, thi, sup,
                                           sdn, col, Y, ldy, R, dinv, s_alpha, part, ps.w, ps.p);
         }
     }
@@ -948,7 +1066,8 @@ __global__ void __launch_bounds__(kThreads, MBL_STAGED_MIN_BLOCKS)
         const LowRec *__restrict__ rp = tbl + spref[p];
         for (uint32_t j0 = warp * RPW; j0 < Rt; j0 += RPB) {
             const uint32_t j = j0 + grp;
-            tile_row_pass<T, V, NB, MODE>(cp, B, X, K, s_tile, K, rp, j, j < Rt, s_meta, tab, hdelta, t0, thi, sup,
+            tile_row_pass<T, V, NB, MODE>(cp, B, X, K, s_tile, K, rp, min(j, Rt - 1u), j < Rt, s_meta, tab, hdelta,
+                                          t0, thi, sup,
                                           sdn, col, Y, K, R, dinv, s_alpha, part, ps.w, ps.p);
         }
         // every read of this tile is done before the next copy overwrites it
@@ -962,15 +1081,15 @@ __global__ void __launch_bounds__(kThreads, MBL_STAGED_MIN_BLOCKS)
 // ---------------------------------------------------------------------------------
 // Streamed tiled product: a few blocks per SM take whole tiles, and every row block the
 // product of a tile reads reaches shared memory by a bulk asynchronous copy.  Each term
-// of a tile's rows is one contiguous block of X: the joining-bond partners (the tile's
-// rows whose boundary spins differ, moved by one rank shift), the wrap partner tile, the
-// tile itself (own rows and in-tile neighbours), and one block per antiparallel high
+// of a tile's rows is one contiguous block of X: the tile itself (own rows and in-tile
+// neighbours), the joining-bond partners (the tile's rows whose boundary spins differ,
+// moved by one rank shift), the wrap partner tile, and one block per antiparallel high
 // bond (the tile's rows moved by that bond's rank shift).  The last warp of the block
 // is the producer: it walks the block's tiles and issues the copies, in that order, into
 // a ring of tile-sized slots (one full and one empty mbarrier per slot), so up to a ring
 // of data is in flight per SM without holding registers.  The other warps consume the
 // slots in the same order, adding each block into per-row accumulators: the sums are
-// formed in the order of the other work orders (joining, wrap, low bonds, high bonds)
+// formed in the order of the other work orders (low bonds, joining, wrap, high bonds)
 // and the result is bitwise that of k_apply_tiled at the same tile width.  PCG launches
 // also stream the rows of r (and w, p) their epilogue reads.  Rows of 32 to 512 bytes
 // (one 32-byte vector per lane), ld = K, 16-byte aligned bases.  Every mbarrier wait is
@@ -1116,12 +1235,12 @@ __global__ void __launch_bounds__(kThreads, kStreamBlocks)
                     ++k;
                     pos.next((uint32_t)nbuf);
                 };
+                issue(X + (int64_t)tm.off * K, Rt);
                 if (jcnt) issue(X + jsrc * K, jcnt);
                 if (cp.periodic && tm.offper != kNoRow) {
                     const int p2 = m - __popc(t ^ (1u << (H - 1)));
                     issue(X + (int64_t)tm.offper * K, binom(sbin, B, p2));
                 }
-                issue(X + (int64_t)tm.off * K, Rt);
                 for (int h = 0; h < tm.nh; ++h) issue(X + ((int64_t)tm.off + (int32_t)tm.shift[h]) * K, Rt);
                 if (MODE == kPcgQ) {
                     issue(R + (int64_t)tm.off * K, Rt);
@@ -1198,33 +1317,7 @@ __global__ void __launch_bounds__(kThreads, kStreamBlocks)
                     pos.next((uint32_t)nbuf);
                 };
                 const T *slot = nullptr;
-                if (jcnt) {
-                    if ((ok = take(slot))) {
-#pragma unroll
-                        for (int pp = 0; pp < P; ++pp)
-                            if (jrow[pp] < Rt && jrow[pp] - jbase < jcnt) {
-                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)(jrow[pp] - jbase) * K + col);
-#pragma unroll
-                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
-                            }
-                        give();
-                    }
-                }
-                if (ok && has_wrap) {
-                    if ((ok = take(slot))) {
-#pragma unroll
-                        for (int pp = 0; pp < P; ++pp) {
-                            const uint32_t u = w0[pp].x & 0xffffu;
-                            if (jrow[pp] < Rt && (u & 1u) != thi) {
-                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)(w0[pp].y & 0xffffu) * K + col);
-#pragma unroll
-                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
-                            }
-                        }
-                        give();
-                    }
-                }
-                if (ok) {
+                {
                     if ((ok = take(slot))) {
 #pragma unroll
                         for (int pp = 0; pp < P; ++pp) {
@@ -1249,6 +1342,32 @@ __global__ void __launch_bounds__(kThreads, kStreamBlocks)
                                 for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
                             }
                             if (MODE == kPcgQ) di[pp] = dinv[off + j];
+                        }
+                        give();
+                    }
+                }
+                if (ok && jcnt) {
+                    if ((ok = take(slot))) {
+#pragma unroll
+                        for (int pp = 0; pp < P; ++pp)
+                            if (jrow[pp] < Rt && jrow[pp] - jbase < jcnt) {
+                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)(jrow[pp] - jbase) * K + col);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
+                            }
+                        give();
+                    }
+                }
+                if (ok && has_wrap) {
+                    if ((ok = take(slot))) {
+#pragma unroll
+                        for (int pp = 0; pp < P; ++pp) {
+                            const uint32_t u = w0[pp].x & 0xffffu;
+                            if (jrow[pp] < Rt && (u & 1u) != thi) {
+                                const Vec<T, V> a = ldv<T, V>(slot + (int64_t)(w0[pp].y & 0xffffu) * K + col);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) nb[pp][v] += a.v[v];
+                            }
                         }
                         give();
                     }
@@ -1564,6 +1683,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(const double *__restrict_
 }
 
 // PCG direction update: w += alpha p_old; p = dinv r + beta p_old (per column scalars).
+// Each thread takes kUpdRows rows of one block slice and requests all their loads before
+// any arithmetic, so that several rows per thread are in flight.
+constexpr int kUpdRows = 4;
 template <typename T, int K, bool WDONE>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(uint32_t n, const T *__restrict__ dinv,
                                                          const T *__restrict__ r, T *__restrict__ p,
@@ -1579,20 +1701,35 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(uint32_t n, const T *__
         bt[v] = (T)ps.beta[col + v];
     }
     const uint32_t rows_per_block = kThreads / G;
-    for (uint32_t row = blockIdx.x * rows_per_block + threadIdx.x / G; row < n;
-         row += gridDim.x * rows_per_block) {
-        const int64_t o = (int64_t)row * K + col;
-        Vec<T, V> rv = ldv<T, V>(r + o), pv = ldv<T, V>(p + o);
-        const T di = dinv[row];
-        if (!WDONE) {  // else the q-launch has done w += alpha p
-            Vec<T, V> wv = ldv<T, V>(w + o);
+    const uint64_t stride = (uint64_t)gridDim.x * rows_per_block * kUpdRows;
+    for (uint64_t base = (uint64_t)blockIdx.x * rows_per_block * kUpdRows + threadIdx.x / G; base < n;
+         base += stride) {
+        Vec<T, V> rv[kUpdRows], pv[kUpdRows], wv[kUpdRows];
+        T di[kUpdRows];
 #pragma unroll
-            for (int v = 0; v < V; ++v) wv.v[v] += a[v] * pv.v[v];
-            stv<T, V>(w + o, wv);
+        for (int q = 0; q < kUpdRows; ++q) {
+            const uint64_t row = base + (uint64_t)q * rows_per_block;
+            const int64_t o = (int64_t)(row < n ? row : n - 1) * K + col;  // a valid row; stored only if < n
+            rv[q] = ldv<T, V>(r + o);
+            pv[q] = ldv<T, V>(p + o);
+            if (!WDONE) wv[q] = ldv<T, V>(w + o);
+            di[q] = dinv[row < n ? row : n - 1];
         }
 #pragma unroll
-        for (int v = 0; v < V; ++v) pv.v[v] = di * rv.v[v] + bt[v] * pv.v[v];
-        stv<T, V>(p + o, pv);
+        for (int q = 0; q < kUpdRows; ++q) {
+            const uint64_t row = base + (uint64_t)q * rows_per_block;
+            if (row >= n) continue;
+            const int64_t o = (int64_t)row * K + col;
+            if (!WDONE) {  // else the q-launch has done w += alpha p
+#pragma unroll
+                for (int v = 0; v < V; ++v) wv[q].v[v] += a[v] * pv[q].v[v];
+                stv<T, V>(w + o, wv[q]);
+            }
+            Vec<T, V> pn;
+#pragma unroll
+            for (int v = 0; v < V; ++v) pn.v[v] = di[q] * rv[q].v[v] + bt[v] * pv[q].v[v];
+            stv<T, V>(p + o, pn);
+        }
     }
 }
 
@@ -2185,18 +2322,20 @@ static cudaError_t pcg_step_k(const ChainParams &cp, uint32_t n, const T *dinv, 
     if (B >= 2) {
         e = launch_tiled<T, K, kPcgT>(cp, B, p, K, t, K, nullptr, dinv, ps, rd, st);
         if (e != cudaSuccess) return e;
-        PcgScalars psq = ps;  // the q-launch also updates w (alpha is known by then)
-        psq.w = w;
-        psq.p = p;
+        PcgScalars psq = ps;
+        if (!MBL_PCG_W_IN_UPDATE) {  // the q-launch also updates w (alpha is known by then)
+            psq.w = w;
+            psq.p = p;
+            wdone = true;
+        }
         e = launch_tiled<T, K, kPcgQ>(cp, B, t, K, nullptr, K, r, dinv, psq, rd, st);
-        wdone = true;
     } else {
         e = launch_apply_k<T, K, kPcgT>(cp, p, K, t, K, n, nullptr, dinv, ps, rd, grid, st);
         if (e != cudaSuccess) return e;
         e = launch_apply_k<T, K, kPcgQ>(cp, t, K, nullptr, K, n, r, dinv, ps, rd, grid, st);
     }
     if (e != cudaSuccess) return e;
-    int ugrid = (int)(((int64_t)n * RowLayout<T, K>::G + kThreads - 1) / kThreads);
+    int ugrid = (int)(((int64_t)n * RowLayout<T, K>::G + kThreads * kUpdRows - 1) / (kThreads * kUpdRows));
     note_launch();
     if (ugrid > num_sms() * 8) ugrid = num_sms() * 8;
     if (wdone) k_pcg_update<T, K, true><<<ugrid, kThreads, 0, st>>>(n, dinv, r, p, w, ps);
