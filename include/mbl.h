@@ -131,31 +131,36 @@ int mbl_set_product_lane_bytes(int k, int dtype, int bytes);
  * per SM; a producer warp copies every row block a tile's product reads -- joining-bond
  * partners, wrap partner tile, the tile, one block per antiparallel high bond, and for the
  * PCG launches the rows of r, w, p -- into a ring of shared-memory slots with bulk
- * asynchronous copies, and the other warps add them up; rows of 32 to 512 bytes).  3 and
- * 4 need ld = k and 16-byte aligned buffers (else persistent).  Results are bitwise
- * identical under every order for the same tile width (mbl_product_tile_width).  Returns
- * MBL_ERR_ARG for schedule outside 0..4, k outside 1..256 or an unknown dtype. */
+ * asynchronous copies, and the other warps add them up; rows of 32 to 512 bytes), 5 = slab
+ * (one block of 288 threads per SM; a producer warp copies every term of a tile's product
+ * -- the tile, its low-pattern records, joining-bond partners, wrap partner tile, one
+ * block per antiparallel high bond, and for the q-launch of the PCG the rows of r -- into
+ * a ring of six 32 KB shared-memory slots; each consumer thread owns one 16-byte column
+ * chunk of up to 8 rows of the tile; rows of 32 to 256 bytes).  3, 4 and 5 need ld = k and
+ * 16-byte aligned buffers (else persistent).  Results are bitwise identical under every
+ * order for the same tile width (mbl_product_tile_width).  Returns MBL_ERR_ARG for
+ * schedule outside 0..5, k outside 1..256 or an unknown dtype. */
 int mbl_set_product_schedule(int k, int dtype, int schedule);
 
-/* Tile width B (>= 2) that work order `schedule` (1..4, as above) uses for a chain of
+/* Tile width B (>= 2) that work order `schedule` (1..5, as above) uses for a chain of
  * length L, block width k and type dtype under the current switches, or 0 when that
  * order has no tiled kernel for this shape (3 and 4 then fall back to persistent, 1 and
  * 2 to the untiled kernel).  Schedule 4 reads the device's shared-memory limit (a CUDA
- * device must be current); 1..3 are host-only.  Returns MBL_ERR_ARG for an unknown dtype,
- * k outside 1..256, L outside 4..32 or schedule outside 1..4. */
+ * device must be current); 1..3 and 5 are host-only.  Returns MBL_ERR_ARG for an unknown
+ * dtype, k outside 1..256, L outside 4..32 or schedule outside 1..5. */
 int mbl_product_tile_width(int L, int dtype, int k, int schedule);
 
 /* Autotuner of the product (the tile widths and work orders above): times the plain
  * product of this chain, block width k, type dtype, under every candidate -- schedule
- * persistent / ordered / staged / streamed (where its conditions hold) times 32- or
- * 64-byte lanes (64 only for rows of >= 64 bytes; streamed has one lane width) -- on the
+ * persistent / ordered / staged / streamed / slab (where its conditions hold) times 32- or
+ * 64-byte lanes (64 only for rows of >= 64 bytes; streamed and slab have one lane width) -- on the
  * caller's buffers X_dev, Y_dev (n x k, ld = k, n = C(L, n_up); X is read, Y
  * overwritten; they must not overlap): one warm-up and `reps` timed launches each
  * (1 <= reps <= 1000), CUDA events on `stream`.  The fastest is kept -- the size-based
  * default of mbl_set_product_schedule unless another candidate is more than 2 % faster
  * -- for all later products with this L, k and dtype in this process (the explicit
  * switches above still take precedence) and reported in *choice (optional): schedule
- * 1..4, lane bytes, tile bits and the mean microseconds per product.  Widths k without a
+ * 1..5, lane bytes, tile bits and the mean microseconds per product.  Widths k without a
  * tiled kernel leave nothing to choose: MBL_OK with *choice zeroed.
  * Host-synchronous (waits for its timing launches). */
 typedef struct {

@@ -237,7 +237,8 @@ def set_product_lane_bytes(k, dtype, nbytes):
 
 
 def set_product_schedule(k, dtype, schedule):
-    """mbl_set_product_schedule: 0 by size, 1 persistent, 2 ordered, 3 staged, 4 streamed."""
+    """mbl_set_product_schedule: 0 by size, 1 persistent, 2 ordered, 3 staged, 4 streamed,
+    5 slab."""
     torch = _torch()
     dt = MBL_F32 if dtype == torch.float32 else MBL_F64
     _check(lib().mbl_set_product_schedule(int(k), dt, int(schedule)), "mbl_set_product_schedule")

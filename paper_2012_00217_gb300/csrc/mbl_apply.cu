@@ -118,28 +118,6 @@ __device__ __forceinline__ void stv(T *p, const Vec<T, V> &x)
     *reinterpret_cast<Vec<T, V> *>(p) = x;
 }
 
-// Load with the streaming (evict-first) hint: for rows that will not be read again while
-// they could still be in L2 (high-bond partners more than kFarBytes away in the vector).
-template <typename T, int V>
-__device__ __forceinline__ Vec<T, V> ldv_stream(const T *p)
-{
-    if constexpr ((V * sizeof(T)) % 16 == 0) {
-        Vec<T, V> x;
-        const float4 *src = reinterpret_cast<const float4 *>(p);
-        float4 *dst = reinterpret_cast<float4 *>(&x);
-#pragma unroll
-        for (int i = 0; i < (int)(V * sizeof(T) / 16); ++i) dst[i] = __ldcs(src + i);
-        return x;
-    } else {
-        return ldv<T, V>(p);
-    }
-}
-
-#ifndef MBL_FAR_BYTES
-#define MBL_FAR_BYTES (48ll << 20)
-#endif
-constexpr long long kFarBytes = MBL_FAR_BYTES;
-
 // Store with the evict-first hint: a product's output is not read again by the same
 // launch, so it should not push the input's rows out of L2.
 template <typename T, int V>
@@ -268,7 +246,7 @@ struct ApplySmem {
 // Reduce per-lane column partials (lanes with equal lane % G share columns) over the
 // block, write this block's k partials, and let the last block finish.  Returns true
 // in the last block (after a __syncthreads, with the block's partial visible).
-template <typename T, int V, int G>
+template <typename T, int V, int G, int NT = kThreads>
 __device__ __forceinline__ bool block_column_reduce(T (*red)[64], T (&part)[V], int k, const Reduce &rd)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -282,7 +260,7 @@ __device__ __forceinline__ bool block_column_reduce(T (*red)[64], T (&part)[V], 
     __syncthreads();
     if (threadIdx.x < k) {
         double acc = 0.0;
-        for (int w = 0; w < kWarps; ++w) acc += (double)red[w][threadIdx.x];
+        for (int w = 0; w < NT / 32; ++w) acc += (double)red[w][threadIdx.x];
         rd.partials[(int64_t)blockIdx.x * k + threadIdx.x] = acc;
     }
     __threadfence();
@@ -300,10 +278,11 @@ __device__ __forceinline__ bool block_column_reduce(T (*red)[64], T (&part)[V], 
 
 // In the last block: total[c] = sum over blocks (fixed order) of partials, using
 // kThreads / k threads per column and a fixed-shape tree.
+template <int NT = kThreads>
 __device__ __forceinline__ void finish_column_sums(const Reduce &rd, int k, double *total)
 {
-    __shared__ double s_tree[kThreads];
-    const int per = kThreads / k;  // threads per column (k divides 256 or per >= 1)
+    __shared__ double s_tree[NT];
+    const int per = NT / k;  // threads per column (k divides 256 or per >= 1)
     const int c = threadIdx.x / per, j = threadIdx.x % per;
     double acc = 0.0;
     if (c < k) {
@@ -342,7 +321,7 @@ __device__ __forceinline__ void finish_column_sums(const Reduce &rd, int k, doub
 // float2 in the partial slots, and only the k final totals are widened to FP64.  The
 // FP64 pipe (about 1/64 of the FP32 rate) would otherwise set a serial tail of
 // several microseconds per launch in the last block.
-template <int V, int G>
+template <int V, int G, int NT = kThreads>
 __device__ __forceinline__ bool block_column_reduce_f32(float (*red)[64], float (&part)[V], int k, const Reduce &rd)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -356,7 +335,7 @@ __device__ __forceinline__ bool block_column_reduce_f32(float (*red)[64], float 
     __syncthreads();
     if (threadIdx.x < k) {
         float sum = 0.0f, cmp = 0.0f;
-        for (int w = 0; w < kWarps; ++w) {
+        for (int w = 0; w < NT / 32; ++w) {
             float hi, e;
             two_sum(sum, red[w][threadIdx.x], hi, e);
             sum = hi;
@@ -377,10 +356,11 @@ __device__ __forceinline__ bool block_column_reduce_f32(float (*red)[64], float 
     return true;
 }
 
+template <int NT = kThreads>
 __device__ __forceinline__ void finish_column_sums_f32(const Reduce &rd, int k, double *total)
 {
-    __shared__ float2 s_tree2[kThreads];
-    const int per = kThreads / k;
+    __shared__ float2 s_tree2[NT];
+    const int per = NT / k;
     const int c = threadIdx.x / per, j = threadIdx.x % per;
     float sum = 0.0f, cmp = 0.0f;
     if (c < k) {
@@ -422,17 +402,17 @@ __device__ __forceinline__ void finish_column_sums_f32(const Reduce &rd, int k, 
     if (threadIdx.x == 0) *rd.counter = 0u;
 }
 
-template <typename T, int V, int G, int MODE>
+template <typename T, int V, int G, int MODE, int NT = kThreads>
 __device__ __forceinline__ void pcg_block_finish(T (*red)[64], T (&part)[V], int K, const PcgScalars &ps,
                                                  const Reduce &rd)
 {
     __shared__ double s_tot[64];
     if constexpr (sizeof(T) == 4) {
-        if (!block_column_reduce_f32<V, G>(red, part, K, rd)) return;
-        finish_column_sums_f32(rd, K, s_tot);
+        if (!block_column_reduce_f32<V, G, NT>(red, part, K, rd)) return;
+        finish_column_sums_f32<NT>(rd, K, s_tot);
     } else {
-        if (!block_column_reduce<T, V, G>(red, part, K, rd)) return;
-        finish_column_sums(rd, K, s_tot);
+        if (!block_column_reduce<T, V, G, NT>(red, part, K, rd)) return;
+        finish_column_sums<NT>(rd, K, s_tot);
     }
     if (threadIdx.x < K) {
         const int c = threadIdx.x;
@@ -599,7 +579,7 @@ static_assert(sizeof(LowRec) == 32, "LowRec layout");
 constexpr int kLowMaxB = 13;  // at most 12 low bonds, C(13, 6) = 1716 rows per tile
 // records for B = 2..13 at offsets 2^B - 4 (the sizes 2^B, B < current, summed)
 constexpr int kLowRecords = (1 << (kLowMaxB + 1)) - 4;
-static __device__ LowRec g_lowtab[kLowRecords];
+static __device__ __align__(16) LowRec g_lowtab[kLowRecords];
 
 __host__ __device__ inline int lowtab_base(int B) { return (1 << B) - 4; }
 
@@ -795,12 +775,7 @@ __device__ __forceinline__ void tile_row_pass(const ChainParams &cp, int B, cons
 #pragma unroll
         for (int e = 0; e < NB; ++e) {
             const int hh = h0 + e < nh ? h0 + e : nh - 1;
-            const int64_t sh = (int64_t)(int32_t)tm.shift[hh] * ldx;
-            // the shift is the same for the whole tile: a uniform choice of hint
-            if ((sh < 0 ? -sh : sh) * (int64_t)sizeof(T) >= kFarBytes)
-                a[e] = ldv_stream<T, V>(xr + sh);
-            else
-                a[e] = ldv<T, V>(xr + sh);
+            a[e] = ldv<T, V>(xr + (int64_t)(int32_t)tm.shift[hh] * ldx);
         }
 #pragma unroll
         for (int e = 0; e < NB; ++e)
@@ -1457,6 +1432,359 @@ __global__ void __launch_bounds__(kThreads, kStreamBlocks)
     }
     if (MODE == kPlain) return;
     pcg_block_finish<T, V, G, MODE>(red, part, K, ps, rd);
+}
+
+// ---------------------------------------------------------------------------------
+// Slab product: every term of a tile's product reaches shared memory as one contiguous
+// block by a bulk asynchronous copy -- the tile itself, the tile's low-pattern records,
+// the joining-bond partner rows, the wrap partner tile, one block per antiparallel high
+// bond, and in the q-launch the tile's rows of r -- through a ring of kSlabSlots slots of
+// 32 KB.  One producer warp per block computes each tile's values (tile_meta_warp) once,
+// records them beside the tile's first slot, and issues the copies; eight consumer warps
+// add the blocks up.  Each consumer thread owns one 16-byte column chunk of up to
+// kSlabPasses rows of the tile (G = row bytes / 16 lanes per row), so every shared-memory
+// read of a row is G x 16 contiguous bytes: no bank conflicts.  A whole ring of data is in
+// flight per SM without holding registers, which is what the L2 needs to deliver rows at
+// its gather bandwidth.  The sums are formed in the order of the other work orders (low
+// bonds, joining, wrap, high bonds): bitwise equal to them at the same tile width.  Every
+// wait is bounded; a timeout stops the producer, drains its copies, and writes NaN to the
+// block's remaining output rows (and its PCG partials).  The q-launch variant leaves
+// w += alpha p to the direction update.
+
+constexpr int kSlabConsumers = 8;
+constexpr int kSlabThreads = 32 * (kSlabConsumers + 1);
+constexpr int kSlabPasses = 8;
+constexpr int kSlabSlotBytes = 32768;
+#ifndef MBL_SLAB_SLOTS
+#define MBL_SLAB_SLOTS 6
+#endif
+constexpr int kSlabSlots = MBL_SLAB_SLOTS;
+
+template <typename T, int K>
+struct SlabLayout {
+    static constexpr int RB = K * (int)sizeof(T);   // row bytes
+    static constexpr int V = 16 / (int)sizeof(T);   // one 16-byte vector per lane
+    static constexpr int G = RB / 16;               // lanes per row
+    static constexpr int RPW = G > 0 ? 32 / G : 1;  // rows per warp and pass
+    static constexpr int RPP = kSlabConsumers * RPW;
+    static constexpr int CAP = kSlabPasses * RPP;   // rows of the largest tile: CAP * RB = 32 KB
+    static constexpr bool ok = RB >= 32 && RB <= 256 && (RB % 16) == 0 && (32 % (RB / 16)) == 0;
+};
+
+// The values of one tile the consumers need, written by the producer with the copy of
+// the tile's own rows (published by that copy's mbarrier).
+template <typename T>
+struct SlabTile {
+    uint32_t off, offper;
+    int nh;
+    T ct;
+};
+
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(kSlabThreads, 1)
+    k_apply_slab(ChainParams cp, int B, const T *__restrict__ X, T *__restrict__ Y, T *__restrict__ R,
+                 const T *__restrict__ dinv, PcgScalars ps, Reduce rd)
+{
+    using SL = SlabLayout<T, K>;
+    constexpr int V = SL::V, G = SL::G, RPW = SL::RPW, RPP = SL::RPP, P = kSlabPasses;
+    constexpr int NS = kSlabSlots;
+    static_assert(SL::ok, "slab rows: 32 to 256 bytes");
+    extern __shared__ __align__(128) unsigned char slab_raw[];
+    __shared__ uint32_t sbin[kBinomDim * kBinomDim];
+    __shared__ T tab[1024];
+    __shared__ T red[kSlabConsumers + 1][64];
+    __shared__ uint32_t spref[kLowMaxB + 2];
+    __shared__ T s_alpha[64];
+    __shared__ TileMeta<T> s_pmeta;         // the producer's scratch
+    __shared__ SlabTile<T> s_tile[NS];      // per slot of a tile's own rows
+    __shared__ __align__(8) uint64_t s_full[NS], s_empty[NS];
+    __shared__ int s_fail;
+    load_binom(sbin);
+    build_field_tables<T>(tab, cp);
+    if (MODE == kPcgQ && threadIdx.x < K) s_alpha[threadIdx.x] = (T)ps.alpha[threadIdx.x];
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&s_full[q], 1);
+            mbar_init(&s_empty[q], kSlabConsumers);
+        }
+        s_fail = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int q = 0; q <= B + 1 && q <= kLowMaxB + 1; ++q) {
+            spref[q] = acc;
+            acc += binom(sbin, B, q);
+        }
+    }
+    __syncthreads();
+
+    const int L = cp.L, m = cp.n_up, H = L - B;
+    const uint32_t ntile = 1u << H;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *fail = &s_fail;
+    const LowRec *__restrict__ tbl = g_lowtab + lowtab_base(B);
+    T part[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) part[v] = (T)0;
+
+    if (warp == kSlabConsumers) {
+        // producer
+        RingPos pos{0u, 0u};
+        uint32_t k = 0;
+        bool ok = true;
+        for (uint32_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            const int p = m - __popc(t);
+            if (p < 0 || p > B) continue;  // warp-uniform
+            __syncwarp();
+            tile_meta_warp<T>(sbin, tab, cp, B, t, p, s_pmeta);
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t Rt = binom(sbin, B, p), c0 = binom(sbin, B - 1, p);
+                const uint32_t sup = p >= 1 ? binom(sbin, B - 1, p - 1) : 0u;
+                const uint32_t t0 = t & 1u;
+                const uint32_t jcnt = t0 ? c0 : Rt - c0;
+                const int64_t jsrc = t0 ? (int64_t)s_pmeta.off - (int64_t)c0 : (int64_t)s_pmeta.off + c0 + sup;
+                auto issue = [&](const void *src, uint32_t bytes, bool own) {
+                    if (!ok) return;
+                    const uint32_t q = pos.s;
+                    // the slot's previous use (one lap ago) must have been released
+                    if (k >= (uint32_t)NS && !ring_wait(&s_empty[q], pos.ph ^ 1u, fail)) {
+                        ok = false;
+                        return;
+                    }
+                    if (own) s_tile[q] = SlabTile<T>{s_pmeta.off, s_pmeta.offper, s_pmeta.nh, s_pmeta.ct};
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&s_full[q], bytes);
+                    bulk_copy_g2s(slab_raw + (size_t)q * kSlabSlotBytes, src, bytes, &s_full[q]);
+                    ++k;
+                    pos.next((uint32_t)NS);
+                };
+                issue(X + (int64_t)s_pmeta.off * K, Rt * (uint32_t)SL::RB, true);
+                issue(tbl + spref[p], Rt * (uint32_t)sizeof(LowRec), false);
+                if (jcnt) issue(X + jsrc * K, jcnt * (uint32_t)SL::RB, false);
+                if (cp.periodic && s_pmeta.offper != kNoRow) {
+                    const int p2 = m - __popc(t ^ (1u << (H - 1)));
+                    issue(X + (int64_t)s_pmeta.offper * K, binom(sbin, B, p2) * (uint32_t)SL::RB, false);
+                }
+                for (int h = 0; h < s_pmeta.nh; ++h)
+                    issue(X + ((int64_t)s_pmeta.off + (int32_t)s_pmeta.shift[h]) * K, Rt * (uint32_t)SL::RB, false);
+                if (MODE == kPcgQ) issue(R + (int64_t)s_pmeta.off * K, Rt * (uint32_t)SL::RB, false);
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        }
+        if (!ok && lane == 0) {
+            // leave no copy in flight: wait (bounded) for the last ring of issued copies
+            const uint32_t k0 = k > (uint32_t)NS ? k - (uint32_t)NS : 0u;
+            for (uint32_t kk = k0; kk < k; ++kk)
+                mbar_wait_bounded(&s_full[kk % (uint32_t)NS], (kk / (uint32_t)NS) & 1u);
+        }
+    } else {
+        // consumers: thread (warp w, row group rw, chunk c) owns rows i * RPP + w * RPW + rw
+        const int rw = lane / G, col = (lane % G) * V;
+        const T hdelta = cp_half_delta<T>(cp);
+        RingPos pos{0u, 0u};
+        bool ok = true;
+        for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+            const int p = m - __popc(t);
+            if (p < 0 || p > B) continue;  // warp-uniform
+            const uint32_t Rt = binom(sbin, B, p), c0 = binom(sbin, B - 1, p);
+            const uint32_t t0 = t & 1u, thi = (t >> (H - 1)) & 1u;
+            const uint32_t jbase = t0 ? 0u : c0, jcnt = t0 ? c0 : Rt - c0;
+            const uint32_t jw0 = (uint32_t)(warp * RPW);
+            auto take = [&](const unsigned char *&slot) -> bool {
+                slot = slab_raw + (size_t)pos.s * kSlabSlotBytes;
+                return __all_sync(0xffffffffu, ring_wait(&s_full[pos.s], pos.ph, fail)) != 0;
+            };
+            auto give = [&]() {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_empty[pos.s]);
+                pos.next((uint32_t)NS);
+            };
+            uint32_t off = 0;
+            if (ok) {
+                const unsigned char *so = nullptr, *sr = nullptr, *sl = nullptr;
+                const uint32_t own_slot = pos.s;
+                ok = take(so);
+                if (ok) {
+                    pos.next((uint32_t)NS);
+                    ok = take(sr);
+                }
+                if (ok) {
+                    const SlabTile<T> st = s_tile[own_slot];
+                    off = st.off;
+                    const bool has_wrap = cp.periodic && st.offper != kNoRow;
+                    const T *__restrict__ own = reinterpret_cast<const T *>(so);
+                    const LowRec *__restrict__ rec = reinterpret_cast<const LowRec *>(sr);
+                    T nb[P][V], dx[P][V];
+                    uint32_t jper[P];
+                    uint32_t wrapbits = 0;
+#pragma unroll
+                    for (int i = 0; i < P; ++i) {
+                        jper[i] = 0;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            nb[i][v] = (T)0;
+                            dx[i][v] = (T)0;
+                        }
+                        if (i * RPP + jw0 >= Rt) continue;  // warp-uniform
+                        const uint32_t j = i * RPP + jw0 + rw;
+                        const bool valid = j < Rt;
+                        const uint32_t jc = valid ? j : Rt - 1u;
+                        const uint4 w0 = reinterpret_cast<const uint4 *>(rec + jc)[0];
+                        const uint4 w1 = reinterpret_cast<const uint4 *>(rec + jc)[1];
+                        const uint32_t u = w0.x & 0xffffu, cnt = (w0.x >> 16) & 0xffu, alow = w0.x >> 24;
+                        const bool join = j - jbase < jcnt;
+                        const bool wrap = has_wrap && (u & 1u) != thi;
+                        jper[i] = w0.y & 0xffffu;
+                        if (valid && wrap) wrapbits |= 1u << i;
+                        // in-tile neighbours, to the largest count of the warp's rows
+                        const uint32_t nbw[6] = {w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                        const int cmax = (int)__reduce_max_sync(0xffffffffu, valid ? cnt : 0u);
+#pragma unroll
+                        for (int q0 = 0; q0 < 12; q0 += 4) {
+                            if (q0 >= cmax) break;
+                            Vec<T, V> a[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int q = q0 + e;
+                                const int qq = q < 12 ? q : 11;
+                                const uint32_t jn = (nbw[qq >> 1] >> (16 * (qq & 1))) & 0xffffu;
+                                a[e] = ldv<T, V>(own + (int64_t)jn * K + col);
+                            }
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (q0 + e < (int)cnt) vadd<T, V>(nb[i], a[e]);
+                        }
+                        const Vec<T, V> x = ldv<T, V>(own + (int64_t)jc * K + col);
+                        const T d = (st.ct + (tab[u & 255u] + tab[256 + (u >> 8)])) -
+                                    mul_rn(hdelta, (T)(alow + (join ? 1u : 0u) + (wrap ? 1u : 0u)));
+                        if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+#pragma unroll
+                            for (int v = 0; v < V; v += 2) {
+                                const float2 r2 = __fmul2_rn(make_float2(d, d), make_float2(x.v[v], x.v[v + 1]));
+                                dx[i][v] = r2.x;
+                                dx[i][v + 1] = r2.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < V; ++v) dx[i][v] = mul_rn(d, x.v[v]);
+                        }
+                    }
+                    // own rows and records are no longer needed
+                    {
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&s_empty[own_slot]);
+                    }
+                    give();
+                    if (jcnt && ok) {
+                        ok = take(sl);
+                        if (ok) {
+                            const T *__restrict__ sj = reinterpret_cast<const T *>(sl);
+#pragma unroll
+                            for (int i = 0; i < P; ++i) {
+                                const uint32_t j = i * RPP + jw0 + rw;
+                                if (i * RPP + jw0 < Rt && j < Rt && j - jbase < jcnt)
+                                    vadd<T, V>(nb[i], ldv<T, V>(sj + (int64_t)(j - jbase) * K + col));
+                            }
+                            give();
+                        }
+                    }
+                    if (has_wrap && ok) {
+                        ok = take(sl);
+                        if (ok) {
+                            const T *__restrict__ sw = reinterpret_cast<const T *>(sl);
+#pragma unroll
+                            for (int i = 0; i < P; ++i)
+                                if ((wrapbits >> i) & 1u) vadd<T, V>(nb[i], ldv<T, V>(sw + (int64_t)jper[i] * K + col));
+                            give();
+                        }
+                    }
+                    for (int h = 0; h < st.nh && ok; ++h) {
+                        ok = take(sl);
+                        if (ok) {
+                            const T *__restrict__ sh = reinterpret_cast<const T *>(sl);
+#pragma unroll
+                            for (int i = 0; i < P; ++i) {
+                                if (i * RPP + jw0 >= Rt) continue;
+                                const uint32_t j = i * RPP + jw0 + rw;
+                                const uint32_t jc = j < Rt ? j : Rt - 1u;
+                                vadd<T, V>(nb[i], ldv<T, V>(sh + (int64_t)jc * K + col));
+                            }
+                            give();
+                        }
+                    }
+                    const T *__restrict__ srr = nullptr;
+                    if (MODE == kPcgQ && ok) {
+                        ok = take(sl);
+                        srr = reinterpret_cast<const T *>(sl);
+                    }
+                    if (ok) {
+                        T alpha[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) alpha[v] = (MODE == kPcgQ) ? s_alpha[col + v] : (T)0;
+#pragma unroll
+                        for (int i = 0; i < P; ++i) {
+                            const uint32_t j = i * RPP + jw0 + rw;
+                            if (i * RPP + jw0 >= Rt || j >= Rt) continue;
+                            T acc[V];
+                            if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+#pragma unroll
+                                for (int v = 0; v < V; v += 2) {
+                                    const float2 r2 = __ffma2_rn(make_float2(0.5f, 0.5f),
+                                                                 make_float2(nb[i][v], nb[i][v + 1]),
+                                                                 make_float2(dx[i][v], dx[i][v + 1]));
+                                    acc[v] = r2.x;
+                                    acc[v + 1] = r2.y;
+                                }
+                            } else {
+#pragma unroll
+                                for (int v = 0; v < V; ++v) acc[v] = fma_rn((T)0.5, nb[i][v], dx[i][v]);
+                            }
+                            const int64_t g = (int64_t)(off + j) * K + col;
+                            Vec<T, V> y;
+                            if (MODE == kPcgQ) {
+                                y = ldv<T, V>(srr + (int64_t)j * K + col);
+                                const T dq = dinv[off + j];
+#pragma unroll
+                                for (int v = 0; v < V; ++v) {
+                                    y.v[v] -= alpha[v] * acc[v];
+                                    part[v] += y.v[v] * (dq * y.v[v]);
+                                }
+                                stv<T, V>(R + g, y);
+                            } else {
+#pragma unroll
+                                for (int v = 0; v < V; ++v) y.v[v] = acc[v];
+                                if (MODE == kPlain) {
+                                    stv_stream<T, V>(Y + g, y);
+                                } else {
+                                    stv<T, V>(Y + g, y);
+#pragma unroll
+                                    for (int v = 0; v < V; ++v) part[v] += acc[v] * acc[v];
+                                }
+                            }
+                        }
+                        if (MODE == kPcgQ) give();
+                    }
+                }
+            }
+            if (!ok) {
+                // the ring stopped: this thread's rows of this and every later tile are NaN
+                // (the tile's first row comes from the tile index, not from the ring)
+                const uint32_t offt = cns_rank(sbin, (t << B) | ((1u << p) - 1u));
+                Vec<T, V> nanv;
+#pragma unroll
+                for (int v = 0; v < V; ++v) nanv.v[v] = (T)NAN;
+                T *dst = (MODE == kPcgQ) ? R : Y;
+                for (uint32_t j = (uint32_t)(jw0 + rw); j < Rt; j += RPP)
+                    stv<T, V>(dst + (int64_t)(offt + j) * K + col, nanv);
+#pragma unroll
+                for (int v = 0; v < V; ++v) part[v] = (T)NAN;
+            }
+        }
+    }
+    if (MODE == kPlain) return;
+    pcg_block_finish<T, V, G, MODE, kSlabThreads>(red, part, K, ps, rd);
 }
 
 // Host side of the low-pattern table: built once per tile width and copied to the
@@ -2155,10 +2483,50 @@ static cudaError_t launch_streamed(const ChainParams &cp, int Bs, const T *X, T 
     return cudaGetLastError();
 }
 
+static bool slab_schedule(int L, int n_up, int K, size_t es) { return schedule_for(L, n_up, K, es) == 5; }
+
+// Tile width of the slab kernel: the widest table-backed B (<= L - 2) whose largest tile
+// fits one 32 KB ring slot (the consumers cover exactly that many rows).
+static int slab_bits(int L, int K, size_t es)
+{
+    const size_t rb = (size_t)K * es;
+    if (rb < 32 || rb > 256 || rb % 16 != 0) return -1;
+    int B = kLowMaxB < L - 2 ? kLowMaxB : L - 2;
+    while (B >= 2 && (size_t)host_binom(B, B / 2) * rb > (size_t)kSlabSlotBytes) --B;
+    return B >= 2 ? B : -1;
+}
+
+template <typename T, int K, int MODE>
+static cudaError_t launch_slab(const ChainParams &cp, int Bs, const T *X, T *Y, T *R, const T *dinv,
+                               const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
+{
+    if (ensure_lowtab(Bs) != MBL_OK) return cudaErrorUnknown;
+    auto kern = k_apply_slab<T, K, MODE>;
+    constexpr int dyn = kSlabSlots * kSlabSlotBytes;
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (attr != cudaSuccess) return attr;
+    const int64_t ntile = (int64_t)1 << (cp.L - Bs);
+    int64_t grid = num_sms();
+    if (grid > ntile) grid = ntile;
+    note_launch();
+    kern<<<(int)grid, kSlabThreads, dyn, st>>>(cp, Bs, X, Y, R, dinv, ps, rd);
+    return cudaGetLastError();
+}
+
 template <typename T, int K, int MODE>
 static cudaError_t launch_tiled(const ChainParams &cp, int B, const T *X, int64_t ldx, T *Y, int64_t ldy, T *R,
                                 const T *dinv, const PcgScalars &ps, const Reduce &rd, cudaStream_t st)
 {
+    if constexpr (SlabLayout<T, K>::ok) {
+        // slab: contiguous rows (ld = K), 16-byte aligned bases for the bulk copies; the
+        // q-launch variant leaves w to the direction update
+        auto al = [](const void *q) { return q == nullptr || (uintptr_t)q % 16 == 0; };
+        if (slab_schedule(cp.L, cp.n_up, K, sizeof(T)) && ldx == K && (Y == nullptr || ldy == K) && al(X) &&
+            al(Y) && al(R) && (MODE != kPcgQ || ps.w == nullptr)) {
+            const int Bs = slab_bits(cp.L, K, sizeof(T));
+            if (Bs >= 2) return launch_slab<T, K, MODE>(cp, Bs, X, Y, R, dinv, ps, rd, st);
+        }
+    }
     if constexpr (StreamLayout<T, K>::ok) {
         // streamed: contiguous rows (ld = K) and 16-byte aligned bases for every streamed block
         auto al = [](const void *q) { return q == nullptr || (uintptr_t)q % 16 == 0; };
@@ -2423,7 +2791,7 @@ extern "C" int mbl_product_tile_width(int L, int dtype, int k, int schedule)
 {
     using namespace mbl;
     if ((dtype != MBL_F32 && dtype != MBL_F64) || k < 1 || k > 256 || L < 4 || L > kMaxL || schedule < 1 ||
-        schedule > 4)
+        schedule > 5)
         return MBL_ERR_ARG;
     const size_t es = dtype == MBL_F32 ? 4 : 8;
     const bool tiled_k = (k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32 || k == 64);
@@ -2432,12 +2800,13 @@ extern "C" int mbl_product_tile_width(int L, int dtype, int k, int schedule)
     int w = B;
     if (schedule == 3) w = (k * (int)es) % 16 == 0 ? staged_bits(L, k, es) : -1;
     if (schedule == 4) w = stream_bits_k(L, k, es);
+    if (schedule == 5) w = (k == 2 || k == 4 || k == 8 || k == 16 || k == 32 || k == 64) ? slab_bits(L, k, es) : -1;
     return w >= 2 ? w : 0;
 }
 
 extern "C" int mbl_set_product_schedule(int k, int dtype, int schedule)
 {
-    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || schedule < 0 || schedule > 4)
+    if (k < 1 || k > 256 || (dtype != MBL_F32 && dtype != MBL_F64) || schedule < 0 || schedule > 5)
         return MBL_ERR_ARG;
     mbl::set_schedule(k, dtype == MBL_F32 ? 4 : 8, schedule);
     return MBL_OK;
@@ -2480,12 +2849,14 @@ extern "C" int mbl_autotune_product(const mbl_chain *chain, int dtype, const voi
     const int def_s = size_schedule(cp.L, cp.n_up, k, es), def_l = rows >= 64 ? size_lane_bytes(k, es) : 32;
     rc = MBL_OK;
     const int sbits = stream_bits_k(cp.L, k, es);
-    for (int sch = 1; sch <= 4 && rc == MBL_OK; ++sch) {
+    const int slbits = slab_bits(cp.L, k, es);
+    for (int sch = 1; sch <= 5 && rc == MBL_OK; ++sch) {
         if (sch == 3 && (rows % 16 != 0 || staged_bits(cp.L, k, es) < 2)) continue;
         if (sch == 4 && sbits < 2) continue;
+        if (sch == 5 && slbits < 2) continue;
         for (int lane = 32; lane <= 64 && rc == MBL_OK; lane *= 2) {
             if (lane == 64 && rows < 64) continue;  // narrower rows: one lane holds the row either way
-            if (lane == 64 && sch == 4) continue;   // the streamed kernel has one lane width
+            if (lane == 64 && (sch == 4 || sch == 5)) continue;  // one lane width there
             t_force_schedule = sch;
             t_force_lane = lane;
             float ms = 0.0f;
@@ -2522,6 +2893,7 @@ extern "C" int mbl_autotune_product(const mbl_chain *chain, int dtype, const voi
         *choice = mbl_product_choice{best_s, best_l,
                                      best_s == 3   ? staged_bits(cp.L, k, es)
                                      : best_s == 4 ? sbits
+                                     : best_s == 5 ? slbits
                                                    : tile_bits_for(cp.L, k, es),
                                      1000.0 * (double)best / reps};
     return MBL_OK;

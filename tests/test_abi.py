@@ -192,7 +192,7 @@ def test_tuning_switches_validate(so):
     for k in (8, 32):
         for dt in (0, 1):
             so.mbl_set_product_lane_bytes(k, dt, 0)
-    for sch, want in ((0, ok), (1, ok), (2, ok), (3, ok), (4, ok), (5, bad), (-1, bad)):
+    for sch, want in ((0, ok), (1, ok), (2, ok), (3, ok), (4, ok), (5, ok), (6, bad), (-1, bad)):
         assert so.mbl_set_product_schedule(64, 0, sch) == want
     so.mbl_set_product_schedule(64, 0, 0)
     for eng, want in ((0, ok), (1, ok), (2, ok), (3, bad), (-1, bad)):
@@ -202,7 +202,8 @@ def test_tuning_switches_validate(so):
 
 def test_tile_width_query_host_schedules(so):
     """mbl_product_tile_width for the host-decided orders: the tile-bits switch for 1 and 2,
-    the widest B <= min(13, L - 2) whose largest tile C(B, B/2) rows fits 48 KB for 3,
+    the widest B <= min(13, L - 2) whose largest tile C(B, B/2) rows fits 48 KB for 3 and
+    32 KB for 5,
     0 where no tiled kernel exists, MBL_ERR_ARG for bad arguments (no device needed)."""
     from math import comb
     from paper_2012_00217_gb300 import binding
@@ -213,6 +214,12 @@ def test_tile_width_query_host_schedules(so):
         while B >= 2 and comb(B, B // 2) * k * es > 48 * 1024:
             B -= 1
         assert so.mbl_product_tile_width(L, dt, k, 3) == B
+        # slab order: the widest B whose largest tile fits one 32 KB ring slot (rows of 32..256 bytes)
+        Bs = min(13, L - 2)
+        while Bs >= 2 and comb(Bs, Bs // 2) * k * es > 32 * 1024:
+            Bs -= 1
+        want = Bs if 32 <= k * es <= 256 else 0
+        assert so.mbl_product_tile_width(L, dt, k, 5) == want
         for bits in (5, 9):
             assert so.mbl_set_product_tile_bits(k, dt, bits) == binding.MBL_OK
             try:
@@ -229,7 +236,7 @@ def test_tile_width_query_host_schedules(so):
     finally:
         so.mbl_set_product_tile_bits(32, 0, 0)
     for L, dt, k, sch in ((3, 0, 8, 1), (33, 0, 8, 1), (20, 2, 8, 1), (20, 0, 0, 1), (20, 0, 257, 1),
-                          (20, 0, 8, 0), (20, 0, 8, 5)):
+                          (20, 0, 8, 0), (20, 0, 8, 6)):
         assert so.mbl_product_tile_width(L, dt, k, sch) == bad
 
 

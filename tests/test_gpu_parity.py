@@ -293,12 +293,16 @@ def test_staged_schedule_full_size_sampled(mbl):
     (13, False, 5, 16, np.float32), (15, True, 4, 32, np.float32), (20, True, 10, 32, np.float32),
     (14, False, 7, 32, np.float64), (16, True, 8, 64, np.float64), (12, True, 6, 4, np.float64),
     (17, True, 8, 16, np.float64), (11, True, 9, 8, np.float64)])
-def test_streamed_schedule_matches_oracle_and_tiled(mbl, L, periodic, n_up, k, dtype):
-    """Schedule 4 (a producer warp streams every row block of a tile's product into a ring
-    of shared-memory slots) against the oracle, and bit for bit against the persistent
-    tiled kernel at the same tile width."""
+@pytest.mark.parametrize("schedule", [4, 5])
+def test_ring_schedules_match_oracle_and_tiled(mbl, L, periodic, n_up, k, dtype, schedule):
+    """Schedules 4 (streamed) and 5 (slab): a producer warp copies every row block of a
+    tile's product into a ring of shared-memory slots.  Against the oracle, and bit for bit
+    against the persistent tiled kernel at the same tile width."""
     tdt = torch.float32 if dtype == np.float32 else torch.float64
-    B = mbl.binding.product_tile_width(L, tdt, k, 4)
+    B = mbl.binding.product_tile_width(L, tdt, k, schedule)
+    if schedule == 5 and not (32 <= k * np.dtype(dtype).itemsize <= 256):
+        assert B == 0  # rows outside the slab kernel's range: persistent instead
+        B = mbl.binding.product_tile_width(L, tdt, k, 1)
     assert B >= 2
     h = wl.fields(L, 7.0, 200 + L + k)
     chain = ham.Chain(L, h, delta=1.1, periodic=periodic, n_up=n_up)
@@ -310,7 +314,7 @@ def test_streamed_schedule_matches_oracle_and_tiled(mbl, L, periodic, n_up, k, d
     Ys = torch.full((n, k), float("nan"), dtype=tdt, device=DEV)
     Yt = torch.full((n, k), float("nan"), dtype=tdt, device=DEV)
     try:
-        mbl.binding.set_product_schedule(k, tdt, 4)
+        mbl.binding.set_product_schedule(k, tdt, schedule)
         mbl.hamiltonian_apply(c, -0.7, Xg, Ys)
         mbl.binding.set_product_schedule(k, tdt, 1)
         mbl.binding.set_product_tile_bits(k, tdt, B)
@@ -324,8 +328,10 @@ def test_streamed_schedule_matches_oracle_and_tiled(mbl, L, periodic, n_up, k, d
     assert np.array_equal(ys, Yt.cpu().numpy())
 
 
-def test_streamed_schedule_full_size_sampled(mbl):
-    """Schedule 4 at L = 26 (k = 32, FP32, periodic): sampled rows against the oracle."""
+@pytest.mark.parametrize("schedule", [4, 5])
+def test_ring_schedules_full_size_sampled(mbl, schedule):
+    """Schedules 4 and 5 at L = 26 (k = 32, FP32, periodic): sampled rows against the
+    oracle."""
     L, k = 26, 32
     h = wl.fields(L, 8.0, 17)
     chain = ham.Chain(L, h, periodic=True)
@@ -335,7 +341,7 @@ def test_streamed_schedule_full_size_sampled(mbl):
     X = torch.randn((n, k), generator=g, device=DEV, dtype=torch.float32)
     Y = torch.empty_like(X)
     try:
-        mbl.binding.set_product_schedule(k, torch.float32, 4)
+        mbl.binding.set_product_schedule(k, torch.float32, schedule)
         mbl.hamiltonian_apply(mbl.make_chain(L, h, 1.0, True), 0.5, X, Y)
     finally:
         mbl.binding.set_product_schedule(k, torch.float32, 0)
@@ -368,7 +374,7 @@ def test_autotune_keeps_a_correct_choice(mbl, L, periodic, k, dtype):
     if k == 3:  # no tiled kernel for this width: nothing to choose
         assert choice["schedule"] == 0
     else:
-        assert choice["schedule"] in (1, 2, 3, 4) and choice["lane_bytes"] in (32, 64)
+        assert choice["schedule"] in (1, 2, 3, 4, 5) and choice["lane_bytes"] in (32, 64)
         assert choice["tile_bits"] >= 2 and choice["microseconds"] > 0
     Xh = X.cpu().numpy()
     mbl.hamiltonian_apply(c, 0.25, X, Y)

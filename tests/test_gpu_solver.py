@@ -193,10 +193,10 @@ def test_not_converged_status(mbl):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("schedule", [3, 4])
+@pytest.mark.parametrize("schedule", [3, 4, 5])
 def test_bulk_copy_schedules_solve_matches_dense(mbl, mode, schedule):
     """The folded LOBPCG with every k = 32 product (PCG launches included) on schedule 3
-    (staged tiles) or 4 (streamed row blocks)."""
+    (staged tiles), 4 (streamed row blocks) or 5 (slab ring)."""
     L = 14
     h = wl.fields(L, 8.0, 1)
     ev = np.linalg.eigvalsh(ham.dense_sector(ham.Chain(L, h, periodic=True)))
