@@ -374,6 +374,52 @@ def batched_sample(torch, mbl, dev, nstreams=16):
                 gap_ratio=gap_ratio_by_w(torch, mbl, dev, ev, len(pick)))
 
 
+def batch_full(args):
+    """--batch-full: the whole disorder-averaging workload -- per W in {2, 4, 8}, 256 x
+    L = 16, 64 x L = 14 and 32 x L = 18 open chains (seeds 0..351), 8 eigenpairs nearest each
+    problem's own spectrum midpoint, mixed precision -- one batched call per W.  Prints one
+    JSON line: eigenpairs/s per W and over the workload, iteration counts, the largest
+    residual, and the adjacent gap ratio of each W's converged levels."""
+    import torch
+    import paper_2012_00217_gb300 as mbl
+    dev = torch.device("cuda:0")
+    mbl.binding.lib()
+    k, nev = BATCH_SAMPLE["k"], BATCH_SAMPLE["nev"]
+    out = dict(workload="352 realizations (256 x L=16, 64 x L=14, 32 x L=18, open) x W in {2,4,8}", nev=nev,
+               k=k, pcg_iters=BATCH_SAMPLE["pcg_iters"], streams=args.batch_streams, per_w={})
+    total_t, total_pairs = 0.0, 0
+    for W in BATCH_SAMPLE["W"]:
+        probs = wl.batched_problems(W)
+        chains = [mbl.make_chain(p["L"], wl.batched_fields(p["L"], W, p["seed"]), p["delta"], p["periodic"])
+                  for p in probs]
+        X0 = torch.cat([torch.from_numpy(wl.initial_block(wl.sector_dim(p["L"]), k, p["seed"])) for p in probs]).to(dev)
+        opts = mbl.make_opts(nev, k, tol=1e-8, max_iter=1000, pcg_iters=BATCH_SAMPLE["pcg_iters"],
+                             mode=mbl.MODE_MIXED)
+        ws = torch.empty(mbl.binding.batched_workspace_size(chains, opts, args.batch_streams), dtype=torch.uint8,
+                         device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, res, stats, rc = mbl.binding.lobpcg_solve_batched(chains, opts, X0, ws, args.batch_streams,
+                                                              allow_not_converged=True)
+        t = time.perf_counter() - t0
+        E = torch.from_numpy(np.ascontiguousarray(ev, dtype=np.float64)).to(dev)
+        r, c = mbl.gap_ratio(E)
+        r, c = r.cpu().numpy(), c.cpu().numpy()
+        okc = c > 0
+        its = [st["iters"] for st in stats]
+        out["per_w"]["W=%g" % W] = dict(
+            seconds=t, eigenpairs_per_s=len(probs) * nev / t, converged=int(sum(st["converged"] for st in stats)),
+            problems=len(probs), iters_mean=float(np.mean(its)), iters_max=int(max(its)),
+            max_rel_resid=float(max(st["max_rel_resid"] for st in stats)),
+            gap_ratio=float((r[okc] * c[okc]).sum() / c[okc].sum()) if okc.any() else None, ratios=int(c.sum()))
+        total_t += t
+        total_pairs += len(probs) * nev
+        del X0, ws, E
+        torch.cuda.empty_cache()
+    out.update(value=total_pairs / total_t, unit="eigenpairs/s", seconds=total_t)
+    print(json.dumps(out))
+
+
 def gap_ratio_by_w(torch, mbl, dev, ev, per_w):
     """Adjacent gap ratio (Sec. 2.2) of the batch's converged levels on the GPU: the mean
     ratio per disorder strength (ratios pooled over that W's problems) and the time of
@@ -434,31 +480,116 @@ def config_l26_iterations(torch, mbl, dev, iters=2):
                 note="stopped after %d iterations: per-iteration time only, not a converged solve" % iters)
 
 
+GOLDEN_L20 = os.path.join(ROOT, "tests", "golden", "l20_periodic_w8_seed1_nearest16.txt")
+
+
+def golden_values(path):
+    """key -> value (evals as a list) of a stored expected-value file under tests/golden/."""
+    out = {"eval": []}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, val = line.split()[:2]
+            if key == "eval":
+                out["eval"].append(float(val))
+            else:
+                out[key] = float(val)
+    return out
+
+
+def oracle_threads():
+    """Threads the oracle's OpenMP loops use in this process."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
 def cpu_baseline(s, gpu_iters, budget_s=20.0):
-    """The oracle as it stands on this host: one LOBPCG iteration of the same workload
-    (bounds + setup + 1 iteration with the same PCG count), extrapolated to the GPU's
-    iteration count; returns eigenpairs/s."""
+    """The oracle as it stands on this host, on a bounded sample of the same workload
+    (L = 20 periodic at its own spectrum midpoint sigma, FP32 Jacobi-PCG inside an FP64
+    LOBPCG as mixed mode runs): one LOBPCG iteration with m_sample of the 640 PCG steps
+    is measured, then scaled by PCG work to 640 steps x the GPU's iteration count.
+    sigma and ||H|| are the stored values of this workload (written by the oracle-only
+    golden script), not the GPU's.  Returns eigenpairs/s."""
     from oracle import hamiltonian as ham
     from oracle import solver
-    threads = os.cpu_count() or 1
+    g = golden_values(GOLDEN_L20)
+    sigma, norm_h = g["sigma"], g["norm_h"]
     ch = ham.Chain(s["L"], s["h"], delta=CFG["delta"], periodic=CFG["periodic"])
     X0 = wl.initial_block(s["n"], s["k"], CFG["seed"])
+    # one FP32 folded product of the block prices a PCG step
     t0 = time.perf_counter()
-    # one matvec to price the rest
-    ham.apply(ch, 0.0, X0[:, :4])
-    t_mv = time.perf_counter() - t0
-    # PCG count reduced so the sample stays within the budget
+    ham.apply(ch, sigma, ham.apply(ch, sigma, X0.astype(np.float32)))
+    t_pcg_step = time.perf_counter() - t0
     m = PCG_ITERS
-    per_iter_est = t_mv / 4 * s["k"] * (2 * m + 8)
-    m_sample = int(max(4, min(m, m * budget_s / max(per_iter_est, 1e-9))))
+    m_sample = int(max(4, min(m, budget_s / max(t_pcg_step, 1e-9))))
     t0 = time.perf_counter()
-    r = solver.lobpcg_folded(ch, 0.0, X0, s["nev"], 1e-30, 1.0, max_iter=1, pcg_iters=m_sample)
+    solver.lobpcg_folded(ch, sigma, X0, s["nev"], 1e-30, norm_h, max_iter=1, pcg_iters=m_sample,
+                         pcg_dtype=np.float32)
     t_sample = time.perf_counter() - t0
-    t_iter = t_sample * (2 * m + 8) / (2 * m_sample + 8)  # scale PCG work to the full count
+    # per iteration: 2 m FP32 block products in the PCG plus 8 FP64 block products
+    t_iter = t_sample * (2 * m + 8) / (2 * m_sample + 8)
     t_solve = t_iter * max(gpu_iters, 1)
-    return dict(value=s["nev"] / t_solve, unit="eigenpairs/s", cores=threads, kind="oracle",
-                sample="1 LOBPCG iteration of the L=20 solve with %d of %d PCG steps (%.1f s), "
-                       "scaled to %d PCG steps x %d iterations" % (m_sample, m, t_sample, m, gpu_iters))
+    return dict(value=s["nev"] / t_solve, unit="eigenpairs/s", cores=oracle_threads(), kind="oracle",
+                measured_s=t_sample, measured_pcg_steps=m_sample, sigma=sigma,
+                extrapolated_s_per_iteration=t_iter,
+                sample="measured: 1 LOBPCG iteration of the L=20 periodic solve at its midpoint sigma with "
+                       "FP32 PCG, %d of %d PCG steps (%.1f s); extrapolated by PCG work to %d steps x %d "
+                       "iterations (%.0f s per solve)" % (m_sample, m, t_sample, m, gpu_iters, t_solve))
+
+
+def cpu_sweep(args):
+    """--cpu-sweep: the oracle's own throughput on this host (no GPU): its block product
+    on the open-chain sweep (GB/s on the algorithmic bytes 2 n k b; median of the timed
+    calls after one warm-up) and whole small solves (eigenpairs/s, measured end to end:
+    spectrum bounds plus the folded LOBPCG).  Prints one JSON line."""
+    import platform
+    from oracle import hamiltonian as ham
+    from oracle import solver
+    thr = oracle_threads()
+    rows = []
+    for L in [int(x) for x in args.cpu_sweep_L.split(",")]:
+        ch = ham.Chain(L, wl.fields(L, 8.0, 0))
+        n = ham.sector_dim(L, L // 2)
+        ham.basis(L, L // 2)
+        for dt, es in ((np.float32, 4), (np.float64, 8)):
+            for k in (1, 8, 32, 64):
+                X = wl.block(n, k, k, dt)
+                ham.apply(ch, 0.0, X)
+                ts = []
+                for _ in range(1 if n * k > 2e8 else 3):
+                    t0 = time.perf_counter()
+                    ham.apply(ch, 0.0, X)
+                    ts.append(time.perf_counter() - t0)
+                t = float(np.median(ts))
+                rows.append(dict(L=L, k=k, dtype="f32" if es == 4 else "f64", s=t, gbs=2.0 * n * k * es / t / 1e9))
+                del X
+    solves = []
+    if not args.cpu_sweep_no_solves:
+        cfg = wl.SOLVE_L12
+        n12 = ham.sector_dim(cfg["L"], cfg["L"] // 2)
+        for name, pcg_dt in (("L12 FP64", np.float64), ("L12 FP32-PCG", np.float32)):
+            ch = ham.Chain(cfg["L"], wl.fields(cfg["L"], cfg["W"], cfg["seed"]))
+            t0 = time.perf_counter()
+            lo, hi = solver.spectrum_bounds(ch, wl.block(n12, 4, 1))
+            r = solver.lobpcg_folded(ch, 0.5 * (lo + hi), wl.initial_block(n12, cfg["k"], cfg["seed"]), cfg["nev"],
+                                     1e-8, max(abs(lo), abs(hi)), max_iter=400, pcg_iters=40, pcg_dtype=pcg_dt)
+            t = time.perf_counter() - t0
+            solves.append(dict(case=name, n=n12, iters=r.iters, converged=bool(r.converged), s=t,
+                               eigenpairs_per_s=cfg["nev"] / t))
+        # one problem of the disorder-averaging batch (L = 14, seed 256, W = 8): bounds + solve
+        L, W, seed = 14, 8.0, 256
+        ch = ham.Chain(L, wl.batched_fields(L, W, seed))
+        n = ham.sector_dim(L, L // 2)
+        t0 = time.perf_counter()
+        lo, hi = solver.spectrum_bounds(ch, wl.block(n, 4, seed))
+        r = solver.lobpcg_folded(ch, 0.5 * (lo + hi), wl.initial_block(n, 16, seed), 8, 1e-8, max(abs(lo), abs(hi)),
+                                 max_iter=400, pcg_iters=240, pcg_dtype=np.float32)
+        t = time.perf_counter() - t0
+        solves.append(dict(case="batch problem L14 W8 seed256 FP32-PCG", n=n, iters=r.iters,
+                           converged=bool(r.converged), s=t, eigenpairs_per_s=8 / t))
+    print(json.dumps({"cpu_sweep": True, "threads": thr, "nproc": os.cpu_count(), "machine": platform.machine(),
+                      "processor": platform.processor(), "matvec": rows, "solves": solves}))
 
 
 def run_reference(args):
@@ -544,6 +675,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the sweep, the batch and the CPU baseline")
+    ap.add_argument("--batch-full", action="store_true",
+                    help="run the whole disorder-averaging workload (3 x 352 problems) and print its figures")
+    ap.add_argument("--batch-streams", type=int, default=16, help="worker streams of --batch-full")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="time the CPU oracle only (product sweep and small whole solves) on this host")
+    ap.add_argument("--cpu-sweep-L", default="22,24,26", help="chain lengths of the oracle product sweep")
+    ap.add_argument("--cpu-sweep-no-solves", action="store_true", help="product sweep only")
     ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
                          "FP32), a short solve (2 iterations x 30 PCG steps), the spectrum bounds or the "
@@ -551,6 +689,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_sweep:
+        return cpu_sweep(args)
+    if args.batch_full:
+        return batch_full(args)
     if args.profile:
         return run_profile(args)
 
