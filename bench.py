@@ -510,12 +510,20 @@ def cpu_baseline(s, gpu_iters, budget_s=20.0):
     LOBPCG as mixed mode runs): one LOBPCG iteration with m_sample of the 640 PCG steps
     is measured, then scaled by PCG work to 640 steps x the GPU's iteration count.
     sigma and ||H|| are the stored values of this workload (written by the oracle-only
-    golden script), not the GPU's.  Returns eigenpairs/s."""
+    golden script; Lanczos on the oracle's sparse matrix if that file is absent), not the
+    GPU's.  Returns eigenpairs/s."""
     from oracle import hamiltonian as ham
     from oracle import solver
-    g = golden_values(GOLDEN_L20)
-    sigma, norm_h = g["sigma"], g["norm_h"]
     ch = ham.Chain(s["L"], s["h"], delta=CFG["delta"], periodic=CFG["periodic"])
+    if os.path.exists(GOLDEN_L20):
+        g = golden_values(GOLDEN_L20)
+        sigma, norm_h = g["sigma"], g["norm_h"]
+    else:  # Lanczos bounds on the oracle's sparse sector matrix (about 10 s)
+        import scipy.sparse.linalg as spla
+        Hs = ham.sparse_sector(ch)
+        lo = float(spla.eigsh(Hs, 1, which="SA", tol=1e-10, return_eigenvectors=False)[0])
+        hi = float(spla.eigsh(Hs, 1, which="LA", tol=1e-10, return_eigenvectors=False)[0])
+        sigma, norm_h = 0.5 * (lo + hi), max(abs(lo), abs(hi))
     X0 = wl.initial_block(s["n"], s["k"], CFG["seed"])
     # one FP32 folded product of the block prices a PCG step
     t0 = time.perf_counter()
