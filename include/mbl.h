@@ -275,19 +275,30 @@ int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, const mbl_lob
 
 /* Batched disorder averaging (Sec. 3.1: realisations and disorder strengths are
  * independent levels of concurrency): nprob problems, any mix of L and fields, solved
- * with the same opts.  nstreams worker threads each drive one CUDA stream and one
- * workspace slot and take problems in order; each problem runs mbl_lobpcg_solve (with
- * captured iterations when opts->use_graph) on its worker's stream, so small problems
- * overlap on the GPU.  The workers start after the work already queued on `stream`, and
- * the call returns when every problem has finished.
+ * with the same opts.  The workspace holds nstreams lanes; each lane solves one problem at
+ * a time, and all lanes advance in lock step on `stream`, one LOBPCG iteration per round:
+ * the steps before and after the preconditioner are enqueued lane by lane, and each of the
+ * pcg_iters PCG steps of all advancing lanes runs as three launches over a table of the
+ * lanes (so a round issues about 40 launches per lane plus 3 per PCG step, not 3 per PCG
+ * step per lane).  When a lane's problem converges (or reaches max_iter) its results are
+ * written and it takes the next problem.  The host synchronises `stream` once per round
+ * to read the lanes' status words.  With opts->use_graph, each lane's steps before and
+ * after the preconditioner are captured once per problem as two small CUDA graphs and
+ * replayed every round; opts->timing is ignored (use_graph = 0 with timing = 1 is
+ * MBL_ERR_ARG).  Every problem's results equal the single-problem solve's to within
+ * rounding (the PCG of a lane runs the same arithmetic in a batched launch; widths k other
+ * than 8, 16, 32, 64 run each lane's own PCG launches and then equal them exactly).
  *   sigmas:   nprob shifts, or NULL: sigma_i = (E_min + E_max)/2 of problem i from
  *             the Lanczos bounds of mbl_spectrum_bounds (tolerance 1e-7, at most 1000
- *             steps, started from column 0 of its X0 block); then, if opts->norm_h <= 0,
+ *             steps, started from column 0 of its X0 block), found before the solves by
+ *             nstreams host threads with a stream and a lane's slot each (started after
+ *             the work already queued on `stream`); then, if opts->norm_h <= 0,
  *             ||H|| = max |E|.
  *   X0_dev:   the problems' n_i x k FP64 start blocks packed one after another.
- *   workspace: mbl_batched_workspace_size bytes (nstreams slots of the largest problem).
+ *   workspace: mbl_batched_workspace_size bytes (nstreams slots of the largest problem and
+ *             the lanes' table).
  *   evals_host, resid_host: nprob x nev (problem-major); evecs_dev: the n_i x nev blocks
- *   packed one after another, or NULL; stats: nprob entries or NULL.
+ *   packed one after another, or NULL; stats: nprob entries or NULL (per-phase times 0).
  * Returns MBL_OK, MBL_ERR_NOT_CONVERGED when some problem did not converge (all outputs
  * written), or the first error met (remaining problems are skipped). */
 int mbl_batched_workspace_size(int nprob, const mbl_chain *chains, const mbl_lobpcg_opts *opts,

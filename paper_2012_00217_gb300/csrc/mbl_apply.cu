@@ -2061,6 +2061,235 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(uint32_t n, const T *__
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Batched PCG step (Sec. 3.1: realizations are independent): one launch covers the PCG
+// phase of many problems ("lanes"), each with its own chain, sector size, tile width,
+// vectors and per-column scalars, read from a table in device memory.  A lane's work
+// items are those of the persistent tiled product (a chunk of rows of one tile); the
+// items of all lanes form rounds of kWarps items, lane after lane, and each block takes a
+// contiguous run of rounds, so a block meets few lanes and rebuilds its shared tables
+// (chain constants, field tables) only when the lane changes.  Each round's column
+// partials (t.t or r.M^-1 r, compensated FP32 pairs in FP32) go to the lane's partials
+// by round; the block that completes a lane's last round sums them in round order and
+// finishes alpha or beta exactly as the single-problem launches do, so the results do not
+// depend on which block ran which round.  The row pass is the shared tile_row_pass.
+
+
+// Last lane whose first round (or row) is <= x: lanes are ordered by both.
+__device__ __forceinline__ int lane_of(const PcgLane *__restrict__ lanes, int nlanes, uint32_t x, bool by_row)
+{
+    int lo = 0, hi = nlanes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const uint32_t v = by_row ? __ldg(&lanes[mid].row0) : __ldg(&lanes[mid].round0);
+        if (v <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int K, int MODE, int LB>
+__global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS)
+    k_pcg_batch(const PcgLane *__restrict__ lanes, int nlanes, uint32_t total_rounds)
+{
+    using Lay = WideRowLayout<T, K, LB>;
+    constexpr int V = Lay::V, G = Lay::G, RPW = 32 / G, CH = Lay::CH;
+    constexpr int NBr = 128 / (V * (int)sizeof(T));
+    constexpr int NB = NBr < 2 ? 2 : (NBr > 8 ? 8 : NBr);
+    __shared__ uint32_t sbin[kBinomDim * kBinomDim];
+    __shared__ T tab[1024];
+    __shared__ T red[kWarps][64];
+    __shared__ uint32_t spref[kLowMaxB + 2];
+    __shared__ T s_alpha[64];
+    __shared__ TileMeta<T> s_meta[kWarps];
+    __shared__ ChainParams s_cp;
+    __shared__ int s_lane;
+    __shared__ unsigned s_last;
+    __shared__ double s_tot[64];
+    load_binom(sbin);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G;
+    const int col = (lane % G) * V;
+    const uint32_t r_begin = (uint32_t)(((uint64_t)total_rounds * blockIdx.x) / gridDim.x);
+    const uint32_t r_end = (uint32_t)(((uint64_t)total_rounds * (blockIdx.x + 1)) / gridDim.x);
+    int cur = -1;
+    for (uint32_t round = r_begin; round < r_end; ++round) {
+        if (threadIdx.x == 0) s_lane = lane_of(lanes, nlanes, round, false);
+        __syncthreads();
+        const int li = s_lane;
+        const PcgLane &Ln = lanes[li];
+        if (li != cur) {
+            // the lane's chain constants, field tables, tile-row prefix and alpha
+            const int *src = reinterpret_cast<const int *>(&Ln.cp);
+            int *dst = reinterpret_cast<int *>(&s_cp);
+            for (int i = threadIdx.x; i < (int)(sizeof(ChainParams) / sizeof(int)); i += kThreads) dst[i] = src[i];
+            __syncthreads();
+            build_field_tables<T>(tab, s_cp);
+            if (MODE == kPcgQ && threadIdx.x < K) s_alpha[threadIdx.x] = (T)Ln.alpha[threadIdx.x];
+            if (threadIdx.x == 0) {
+                const int B = Ln.B;
+                uint32_t acc = 0;
+                for (int q = 0; q <= B + 1 && q <= kLowMaxB + 1; ++q) {
+                    spref[q] = acc;
+                    acc += binom(sbin, B, q);
+                }
+            }
+            __syncthreads();
+            cur = li;
+        }
+        const ChainParams &cp = s_cp;
+        const int B = Ln.B;
+        const int L = cp.L, m = cp.n_up, H = L - B;
+        const uint32_t nchunk = (binom(sbin, B, B / 2) + CH - 1) / CH;
+        const T hdelta = cp_half_delta<T>(cp);
+        T *__restrict__ X = (T *)(MODE == kPcgT ? Ln.p : Ln.t);
+        T *__restrict__ Y = (T *)(MODE == kPcgT ? Ln.t : nullptr);
+        T *__restrict__ R = (T *)(MODE == kPcgQ ? Ln.r : nullptr);
+        const T *__restrict__ dinv = (const T *)Ln.dinv;
+        T part[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) part[v] = (T)0;
+        const uint32_t item = (round - Ln.round0) * kWarps + warp;
+        if (item < Ln.items) {
+            const uint32_t t = item / nchunk, c = item % nchunk;
+            const int p = m - __popc(t);
+            const uint32_t Rt = (p >= 0 && p <= B) ? binom(sbin, B, p) : 0u;
+            const uint32_t j_begin = c * CH;
+            if (j_begin < Rt) {  // warp-uniform
+                const uint32_t j_end = min(Rt, j_begin + CH);
+                TileMeta<T> &tm = s_meta[warp];
+                __syncwarp();
+                tile_meta_warp<T>(sbin, tab, cp, B, t, p, tm);
+                __syncwarp();
+                const uint32_t t0 = t & 1u, thi = (t >> (H - 1)) & 1u;
+                const uint32_t sup = p >= 1 ? binom(sbin, B - 1, p - 1) : 0u;
+                const uint32_t sdn = binom(sbin, B - 1, p);
+                const LowRec *__restrict__ rp = g_lowtab + lowtab_base(B) + spref[p];
+                const T *__restrict__ Xt = X + (int64_t)tm.off * K;
+                for (uint32_t j0 = j_begin; j0 < j_end; j0 += RPW) {
+                    const uint32_t j = j0 + grp;
+                    tile_row_pass<T, V, NB, MODE>(cp, B, X, K, Xt, K, rp, min(j, j_end - 1u), j < j_end, tm, tab,
+                                                  hdelta, t0, thi, sup, sdn, col, Y, K, R, dinv, s_alpha, part,
+                                                  nullptr, nullptr);
+                }
+            }
+        }
+        // this round's column partials -> the lane's partial slot of the round
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            for (int off = G; off < 32; off <<= 1) part[v] += __shfl_xor_sync(0xffffffffu, part[v], off);
+        if (lane < G) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) red[warp][lane * V + v] = part[v];
+        }
+        __syncthreads();
+        const uint32_t slot = round - Ln.round0;
+        if (threadIdx.x < K) {
+            if constexpr (sizeof(T) == 4) {
+                float sum = 0.0f, cmp = 0.0f;
+                for (int w = 0; w < kWarps; ++w) {
+                    float hi, e;
+                    two_sum(sum, red[w][threadIdx.x], hi, e);
+                    sum = hi;
+                    cmp += e;
+                }
+                reinterpret_cast<float2 *>(Ln.partials)[(int64_t)slot * K + threadIdx.x] = make_float2(sum, cmp);
+            } else {
+                double acc = 0.0;
+                for (int w = 0; w < kWarps; ++w) acc += (double)red[w][threadIdx.x];
+                Ln.partials[(int64_t)slot * K + threadIdx.x] = acc;
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(Ln.counter, 1u) == Ln.nrounds - 1) ? 1u : 0u;
+        __syncthreads();
+        if (s_last) {
+            // this block finished the lane's last round: sum the rounds in order
+            __threadfence();
+            if (threadIdx.x < K) {
+                double tot;
+                if constexpr (sizeof(T) == 4) {
+                    const float2 *pp = reinterpret_cast<const float2 *>(Ln.partials);
+                    float S = 0.0f, C = 0.0f;
+                    for (uint32_t q = 0; q < Ln.nrounds; ++q) {
+                        const float2 v2 = pp[(int64_t)q * K + threadIdx.x];
+                        float hi, e;
+                        two_sum(S, v2.x, hi, e);
+                        S = hi;
+                        C += e + v2.y;
+                    }
+                    tot = (double)S + (double)C;
+                } else {
+                    double S = 0.0;
+                    for (uint32_t q = 0; q < Ln.nrounds; ++q) S += Ln.partials[(int64_t)q * K + threadIdx.x];
+                    tot = S;
+                }
+                const int cc = threadIdx.x;
+                if (MODE == kPcgT) {
+                    const bool ok = Ln.active[cc] && tot > 0.0 && isfinite(tot);
+                    Ln.alpha[cc] = ok ? Ln.rz[cc] / tot : 0.0;
+                } else {
+                    int act = Ln.active[cc];
+                    if (!isfinite(tot)) act = 0;
+                    if (Ln.tol2 > 0.0 && tot <= Ln.tol2 * Ln.rz0[cc]) act = 0;
+                    Ln.beta[cc] = (act && Ln.rz[cc] > 0.0) ? tot / Ln.rz[cc] : 0.0;
+                    if (!act) Ln.alpha[cc] = 0.0;
+                    Ln.active[cc] = act;
+                    Ln.rz[cc] = tot;
+                }
+            }
+            if (threadIdx.x == 0) *Ln.counter = 0u;
+        }
+    }
+}
+
+// Batched direction update: w += alpha p, p = M^-1 r + beta p for every lane's rows (the
+// lanes' rows concatenated; each thread takes kUpdRows rows, loads first).
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) k_pcg_batch_update(const PcgLane *__restrict__ lanes, int nlanes,
+                                                               uint32_t total_rows)
+{
+    using Lay = RowLayout<T, K>;
+    constexpr int V = Lay::V, G = Lay::G;
+    const int col = (threadIdx.x % G) * V;
+    const uint32_t rows_per_block = kThreads / G;
+    const uint64_t stride = (uint64_t)gridDim.x * rows_per_block * kUpdRows;
+    for (uint64_t base = (uint64_t)blockIdx.x * rows_per_block * kUpdRows + threadIdx.x / G; base < total_rows;
+         base += stride) {
+        Vec<T, V> rv[kUpdRows], pv[kUpdRows], wv[kUpdRows];
+        T di[kUpdRows];
+        int li[kUpdRows];
+        int64_t o[kUpdRows];
+#pragma unroll
+        for (int q = 0; q < kUpdRows; ++q) {
+            uint64_t row = base + (uint64_t)q * rows_per_block;
+            if (row >= total_rows) row = total_rows - 1;  // a valid row; stored only if in range
+            li[q] = lane_of(lanes, nlanes, (uint32_t)row, true);
+            const PcgLane &Ln = lanes[li[q]];
+            const uint32_t lr = (uint32_t)row - Ln.row0;
+            o[q] = (int64_t)lr * K + col;
+            rv[q] = ldv<T, V>((const T *)Ln.r + o[q]);
+            pv[q] = ldv<T, V>((const T *)Ln.p + o[q]);
+            wv[q] = ldv<T, V>((const T *)Ln.w + o[q]);
+            di[q] = ((const T *)Ln.dinv)[lr];
+        }
+#pragma unroll
+        for (int q = 0; q < kUpdRows; ++q) {
+            if (base + (uint64_t)q * rows_per_block >= total_rows) continue;
+            const PcgLane &Ln = lanes[li[q]];
+            Vec<T, V> pn;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T a = (T)Ln.alpha[col + v], bt = (T)Ln.beta[col + v];
+                wv[q].v[v] += a * pv[q].v[v];
+                pn.v[v] = di[q] * rv[q].v[v] + bt * pv[q].v[v];
+            }
+            stv<T, V>((T *)Ln.w + o[q], wv[q]);
+            stv<T, V>((T *)Ln.p + o[q], pn);
+        }
+    }
+}
+
 // Generic-k version of the PCG product kernels (one warp per row, lanes stride the
 // columns, k <= 64).
 template <typename T, int MODE>
@@ -2679,6 +2908,86 @@ template int pcg_start<float>(const double *, int64_t, const double *, uint32_t,
                               float *, float *, const PcgDev &, cudaStream_t);
 template int pcg_start<double>(const double *, int64_t, const double *, uint32_t, int, const double *, double *,
                                double *, double *, const PcgDev &, cudaStream_t);
+
+// ---- batched PCG step: host side ------------------------------------------------
+
+// Work items and rounds of one lane (the persistent tiled product's items: a chunk of
+// WideRowLayout::CH rows of one tile, all 2^(L-B) tiles).
+template <typename T, int K>
+static void lane_items(int L, int B, uint32_t *items, uint32_t *nrounds)
+{
+    constexpr int CH = WideRowLayout<T, K, 32>::CH;
+    const uint32_t nchunk = (host_binom(B, B / 2) + CH - 1) / CH;
+    *items = (uint32_t)(((uint64_t)1 << (L - B)) * nchunk);
+    *nrounds = (*items + kWarps - 1) / kWarps;
+}
+
+int pcg_lane_fill(PcgLane *Ln, const ChainParams &cp, uint32_t n, int k, int f32, const void *dinv, void *r,
+                  void *p, void *t, void *w, const PcgDev &pd, uint32_t *round0, uint32_t *row0)
+{
+    const size_t es = f32 ? 4 : 8;
+    const int B = tile_bits_for(cp.L, k, es);
+    if (B < 2) return MBL_ERR_ARG;
+    if (ensure_lowtab(B) != MBL_OK) return MBL_ERR_CUDA;
+    uint32_t items = 0, nrounds = 0;
+    switch (k) {
+    case 8: f32 ? lane_items<float, 8>(cp.L, B, &items, &nrounds) : lane_items<double, 8>(cp.L, B, &items, &nrounds); break;
+    case 16: f32 ? lane_items<float, 16>(cp.L, B, &items, &nrounds) : lane_items<double, 16>(cp.L, B, &items, &nrounds); break;
+    case 32: f32 ? lane_items<float, 32>(cp.L, B, &items, &nrounds) : lane_items<double, 32>(cp.L, B, &items, &nrounds); break;
+    case 64: f32 ? lane_items<float, 64>(cp.L, B, &items, &nrounds) : lane_items<double, 64>(cp.L, B, &items, &nrounds); break;
+    default: return MBL_ERR_ARG;
+    }
+    // the lane's round partials live in its PCG partials buffer
+    if ((size_t)nrounds * k > pcg_partial_doubles()) return MBL_ERR_ARG;
+    *Ln = PcgLane{cp, dinv, r, p, t, w, pd.rz, pd.rz0, pd.alpha, pd.beta, pd.active, pd.tol2, pd.partials,
+                  pd.counter, n, B, items, *round0, nrounds, *row0};
+    *round0 += nrounds;
+    *row0 += n;
+    return MBL_OK;
+}
+
+template <typename T, int K>
+static cudaError_t pcg_batch_step_k(const PcgLane *lanes, int nlanes, uint32_t rounds, uint32_t rows, cudaStream_t st)
+{
+    static const int per_sm = [&]() {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pcg_batch<T, K, kPcgT, 32>, kThreads, 0) != cudaSuccess ||
+            v < 1)
+            v = 1;
+        return v;
+    }();
+    int64_t grid = (int64_t)num_sms() * per_sm;
+    if (grid > rounds) grid = rounds;
+    note_launch();
+    k_pcg_batch<T, K, kPcgT, 32><<<(int)grid, kThreads, 0, st>>>(lanes, nlanes, rounds);
+    note_launch();
+    k_pcg_batch<T, K, kPcgQ, 32><<<(int)grid, kThreads, 0, st>>>(lanes, nlanes, rounds);
+    int ugrid = (int)(((int64_t)rows * RowLayout<T, K>::G + kThreads * kUpdRows - 1) / (kThreads * kUpdRows));
+    if (ugrid > num_sms() * 8) ugrid = num_sms() * 8;
+    if (ugrid < 1) ugrid = 1;
+    note_launch();
+    k_pcg_batch_update<T, K><<<ugrid, kThreads, 0, st>>>(lanes, nlanes, rows);
+    return cudaGetLastError();
+}
+
+int pcg_batch_step(int f32, const PcgLane *lanes_dev, int nlanes, int k, uint32_t rounds, uint32_t rows,
+                   cudaStream_t st)
+{
+    if (nlanes < 1 || rounds < 1 || rows < 1) return MBL_ERR_ARG;
+    cudaError_t e;
+    switch (k) {
+    case 8: e = f32 ? pcg_batch_step_k<float, 8>(lanes_dev, nlanes, rounds, rows, st)
+                    : pcg_batch_step_k<double, 8>(lanes_dev, nlanes, rounds, rows, st); break;
+    case 16: e = f32 ? pcg_batch_step_k<float, 16>(lanes_dev, nlanes, rounds, rows, st)
+                     : pcg_batch_step_k<double, 16>(lanes_dev, nlanes, rounds, rows, st); break;
+    case 32: e = f32 ? pcg_batch_step_k<float, 32>(lanes_dev, nlanes, rounds, rows, st)
+                     : pcg_batch_step_k<double, 32>(lanes_dev, nlanes, rounds, rows, st); break;
+    case 64: e = f32 ? pcg_batch_step_k<float, 64>(lanes_dev, nlanes, rounds, rows, st)
+                     : pcg_batch_step_k<double, 64>(lanes_dev, nlanes, rounds, rows, st); break;
+    default: return MBL_ERR_ARG;
+    }
+    return e == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
 
 template <typename T, int K>
 static cudaError_t pcg_step_k(const ChainParams &cp, uint32_t n, const T *dinv, T *r, T *p, T *t, T *w,

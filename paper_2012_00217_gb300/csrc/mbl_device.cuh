@@ -106,6 +106,25 @@ struct ChainParams {
     float half_delta_f, diag_const_f;  // rounded once
 };
 
+// One problem (lane) of a batched PCG launch: its chain, vectors, per-column scalars and
+// its place in the launch's rounds and concatenated rows (filled by pcg_lane_fill).
+struct PcgLane {
+    ChainParams cp;
+    const void *dinv;
+    void *r, *p, *t, *w;
+    double *rz, *rz0, *alpha, *beta;
+    int *active;
+    double tol2;
+    double *partials;   // >= nrounds * 64 doubles
+    unsigned *counter;  // zero between launches (the finishing block resets it)
+    uint32_t n;
+    int B;              // tile width
+    uint32_t items;     // work items of the lane
+    uint32_t round0;    // first round of the lane
+    uint32_t nrounds;   // ceil(items / kWarps)
+    uint32_t row0;      // first row of the lane in the concatenated rows (update launch)
+};
+
 // The chain constants in the kernel's own type.
 template <typename T>
 __device__ __forceinline__ T cp_diag_const(const ChainParams &cp);

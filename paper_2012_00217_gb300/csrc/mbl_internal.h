@@ -55,6 +55,14 @@ int pcg_start(const double *B, int64_t ldb, const double *bnorm, uint32_t n, int
 template <typename T>
 int pcg_step(const ChainParams &cp, uint32_t n, int k, const T *dinv, T *r, T *p, T *t, T *w, const PcgDev &pd,
              cudaStream_t st);
+// Batched PCG step over nlanes problems (lanes_dev: a device copy of PcgLane entries filled
+// by pcg_lane_fill, in round order); every lane has block width k, FP32 (f32) or FP64
+// vectors.  Three launches for all lanes.
+struct PcgLane;
+int pcg_lane_fill(PcgLane *lane, const ChainParams &cp, uint32_t n, int k, int f32, const void *dinv, void *r,
+                  void *p, void *t, void *w, const PcgDev &pd, uint32_t *round0, uint32_t *row0);
+int pcg_batch_step(int f32, const PcgLane *lanes_dev, int nlanes, int k, uint32_t rounds, uint32_t rows,
+                   cudaStream_t st);
 
 uint32_t host_binom(int n, int k);
 

@@ -252,32 +252,46 @@ struct Solver {
         MBL_TRY(colnorms(b.Tmp, k, k, n, b.rn, 1, b.part, st));
         return MBL_OK;
     }
-    // Steps 2..8 (+ the status of the next iteration).
-    int enqueue_body(bool have_p)
+    PcgDev pcg_dev() const
     {
-        // 2. residual of the current block
+        return PcgDev{b.pcg_s, b.pcg_s + 64, b.pcg_s + 128, b.pcg_s + 192, b.pcg_active, pcg_tol * pcg_tol,
+                      b.pcg_part, b.counter};
+    }
+    // Step 2 and the start of step 3: the residual of the current block and, folded, the
+    // PCG start from its normalised columns.
+    int enqueue_pre_pcg()
+    {
         mark(0);
         MBL_TRY(gram(X(), ld3(), k, AX(), ld3(), k, n, b.Gk, k, 1, gmix, b.part, st));
         MBL_TRY(update(X(), ld3(), k, b.Gk, k, k, AX(), ld3(), b.Tmp, k, n, -1.0, 1.0, 0, st));
         mark(1);
+        if (!folded) return MBL_OK;
+        MBL_TRY(colnorms(b.Tmp, k, k, n, b.rn, 1, b.part, st));
+        const PcgDev pd = pcg_dev();
+        if (mixed)
+            return pcg_start<float>(b.Tmp, k, b.rn, (uint32_t)n, k, (const float *)b.dinv, (float *)b.pr,
+                                    (float *)b.pp, (float *)b.pw, pd, st);
+        return pcg_start<double>(b.Tmp, k, b.rn, (uint32_t)n, k, (const double *)b.dinv, (double *)b.pr,
+                                 (double *)b.pp, (double *)b.pw, pd, st);
+    }
+    // Step 3: the m PCG steps of this problem alone.
+    int enqueue_pcg_steps()
+    {
+        const PcgDev pd = pcg_dev();
+        for (int it = 0; it < m; ++it) {
+            if (mixed)
+                MBL_TRY(pcg_step<float>(cp, (uint32_t)n, k, (const float *)b.dinv, (float *)b.pr, (float *)b.pp,
+                                        (float *)b.pt, (float *)b.pw, pd, st));
+            else
+                MBL_TRY(pcg_step<double>(cp, (uint32_t)n, k, (const double *)b.dinv, (double *)b.pr,
+                                         (double *)b.pp, (double *)b.pt, (double *)b.pw, pd, st));
+        }
+        return MBL_OK;
+    }
+    // Steps 4..8 (+ the status of the next iteration), after the preconditioner.
+    int enqueue_post_pcg(bool have_p)
+    {
         if (folded) {
-            // 3. preconditioner
-            MBL_TRY(colnorms(b.Tmp, k, k, n, b.rn, 1, b.part, st));
-            PcgDev pd{b.pcg_s, b.pcg_s + 64, b.pcg_s + 128, b.pcg_s + 192, b.pcg_active, pcg_tol * pcg_tol,
-                      b.pcg_part, b.counter};
-            if (mixed) {
-                MBL_TRY(pcg_start<float>(b.Tmp, k, b.rn, (uint32_t)n, k, (const float *)b.dinv, (float *)b.pr,
-                                         (float *)b.pp, (float *)b.pw, pd, st));
-                for (int it = 0; it < m; ++it)
-                    MBL_TRY(pcg_step<float>(cp, (uint32_t)n, k, (const float *)b.dinv, (float *)b.pr, (float *)b.pp,
-                                            (float *)b.pt, (float *)b.pw, pd, st));
-            } else {
-                MBL_TRY(pcg_start<double>(b.Tmp, k, b.rn, (uint32_t)n, k, (const double *)b.dinv, (double *)b.pr,
-                                          (double *)b.pp, (double *)b.pw, pd, st));
-                for (int it = 0; it < m; ++it)
-                    MBL_TRY(pcg_step<double>(cp, (uint32_t)n, k, (const double *)b.dinv, (double *)b.pr,
-                                             (double *)b.pp, (double *)b.pt, (double *)b.pw, pd, st));
-            }
             matvecs += (int64_t)2 * m * k;
             MBL_TRY(widen(mixed, b.pw, k, W(), ld3(), k, n, st));
         } else {
@@ -315,6 +329,13 @@ struct Solver {
         MBL_TRY(folded ? enqueue_hrr() : enqueue_bounds_status());
         mark(8);
         return MBL_OK;
+    }
+    // Steps 2..8 (+ the status of the next iteration).
+    int enqueue_body(bool have_p)
+    {
+        MBL_TRY(enqueue_pre_pcg());
+        if (folded) MBL_TRY(enqueue_pcg_steps());
+        return enqueue_post_pcg(have_p);
     }
     // Directions below the resolution of the Gram matrix are dropped: its entries carry
     // FP32 rounding in mixed mode.
@@ -429,35 +450,16 @@ int run_body(Solver &s, bool have_p, bool use_graph, GraphCache &gc)
     return MBL_OK;
 }
 
-}  // namespace
-
-}  // namespace mbl
-
-using namespace mbl;
-
-extern "C" int mbl_lobpcg_workspace_size(const mbl_chain *chain, const mbl_lobpcg_opts *opts, size_t *bytes)
+// Everything before the first iteration, enqueued on st: the workspace carve-up, the
+// sector basis, the norm of the tolerance (a Gershgorin bound, read back with a host
+// synchronisation, when opts->norm_h <= 0), the preconditioner diagonal, and the start
+// block orthonormalised and rotated onto A's Ritz vectors with its first H Rayleigh-Ritz
+// status.
+int solver_setup(Solver &s, const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts, int64_t n,
+                 const double *X0_dev, void *workspace_dev, size_t workspace_bytes, cudaStream_t st)
 {
-    int64_t n;
-    if (!bytes) return MBL_ERR_ARG;
-    int rc = check_opts(chain, opts, &n);
-    if (rc != MBL_OK) return rc;
-    carve(nullptr, n, opts->k, opts->mode == MBL_MODE_MIXED, bytes);
-    return MBL_OK;
-}
-
-extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
-                                const double *X0_dev, void *workspace_dev, size_t workspace_bytes,
-                                double *evals_host, double *evecs_dev, double *resid_host, mbl_lobpcg_stats *stats,
-                                mbl_stream_t stream)
-{
-    auto t0 = std::chrono::steady_clock::now();
-    int64_t n;
-    int rc = check_opts(chain, opts, &n);
-    if (rc != MBL_OK) return rc;
-    if (!X0_dev || !workspace_dev) return MBL_ERR_ARG;
-    if ((uintptr_t)workspace_dev % kAlign) return MBL_ERR_ARG;
-    Solver s;
-    rc = make_chain_params(chain, sigma, &s.cp);
+    const mbl_stream_t stream = (mbl_stream_t)st;
+    int rc = make_chain_params(chain, sigma, &s.cp);
     if (rc != MBL_OK) return rc;
     size_t need = 0;
     const int mixed = opts->mode == MBL_MODE_MIXED;
@@ -472,9 +474,9 @@ extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_
     s.largest = 0;
     s.folded = 1;
     s.pcg_tol = opts->pcg_tol;
-    s.st = (cudaStream_t)stream;
+    s.st = st;
+    s.matvecs = 0;
     const int k = s.k;
-
     if (cudaMemsetAsync(s.b.counter, 0, 4 * sizeof(unsigned), s.st) != cudaSuccess ||
         cudaMemsetAsync(s.b.iflags, 0, (16 + 64) * sizeof(int), s.st) != cudaSuccess)
         return MBL_ERR_CUDA;
@@ -513,6 +515,46 @@ extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_
     MBL_TRY(initial_rr(s));
     MBL_TRY(s.enqueue_hrr());
     if (s.timing) cudaEventRecord(s.ev[0], s.st);
+    return MBL_OK;
+}
+
+}  // namespace
+
+}  // namespace mbl
+
+using namespace mbl;
+
+extern "C" int mbl_lobpcg_workspace_size(const mbl_chain *chain, const mbl_lobpcg_opts *opts, size_t *bytes)
+{
+    int64_t n;
+    if (!bytes) return MBL_ERR_ARG;
+    int rc = check_opts(chain, opts, &n);
+    if (rc != MBL_OK) return rc;
+    carve(nullptr, n, opts->k, opts->mode == MBL_MODE_MIXED, bytes);
+    return MBL_OK;
+}
+
+extern "C" int mbl_lobpcg_solve(const mbl_chain *chain, double sigma, const mbl_lobpcg_opts *opts,
+                                const double *X0_dev, void *workspace_dev, size_t workspace_bytes,
+                                double *evals_host, double *evecs_dev, double *resid_host, mbl_lobpcg_stats *stats,
+                                mbl_stream_t stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    int64_t n;
+    int rc = check_opts(chain, opts, &n);
+    if (rc != MBL_OK) return rc;
+    if (!X0_dev || !workspace_dev) return MBL_ERR_ARG;
+    if ((uintptr_t)workspace_dev % kAlign) return MBL_ERR_ARG;
+    Solver s;
+    rc = solver_setup(s, chain, sigma, opts, n, X0_dev, workspace_dev, workspace_bytes, (cudaStream_t)stream);
+    if (rc != MBL_OK) {
+        if (s.timing)
+            for (auto &e : s.ev)
+                if (e) cudaEventDestroy(e);
+        return rc;
+    }
+    const int k = s.k;
+    const double norm_h = s.norm_h;
 
     HostStatus hs;
     GraphCache gc;
@@ -697,10 +739,15 @@ extern "C" int mbl_lobpcg_solve_noalloc(const mbl_chain *chain, double sigma, co
 }
 
 // ------------------------------------------------------------------------------------
-// Batched solve: many disorder realisations (any mix of L) in flight at once.  Each of
-// nstreams worker threads owns a stream and one workspace slot, takes the next problem,
-// finds sigma and ||H|| from its spectrum bounds when they are not given, and runs the
-// single-problem solve (whose iterations are captured CUDA graphs) on its stream.
+// Batched solve: many disorder realisations (any mix of L) advanced in lock step.  The
+// workspace holds nlanes slots; each lane solves one problem at a time, and every round
+// advances every lane by one LOBPCG iteration on the caller's stream: the steps before
+// and after the preconditioner are enqueued lane by lane, and the m PCG steps of all
+// lanes run as three launches per step over a table of the lanes (pcg_batch_step).  A
+// lane whose problem has converged (or reached max_iter) writes its results and takes
+// the next problem.  The host synchronises once per round and reads each lane's status
+// words.  When no shifts are given, each problem's spectrum bounds are found first by
+// nlanes host threads, one stream and one slot each.
 
 namespace {
 
@@ -724,54 +771,23 @@ size_t batch_slot_bytes(int nprob, const mbl_chain *chains, const mbl_lobpcg_opt
     return align_up(slot);
 }
 
-}  // namespace
+size_t batch_table_bytes(int nlanes) { return align_up((size_t)nlanes * sizeof(PcgLane)); }
 
-extern "C" int mbl_batched_workspace_size(int nprob, const mbl_chain *chains, const mbl_lobpcg_opts *opts,
-                                          int nstreams, size_t *bytes)
+// sigma_i and ||H||_i of every problem from its own Lanczos bounds, nth host threads.
+int batch_bounds(int nprob, const mbl_chain *chains, const double *X0_dev, const std::vector<int64_t> &off_x,
+                 int k, void *workspace_dev, size_t slot, int nth, cudaStream_t after, double norm_given,
+                 std::vector<double> &sig, std::vector<double> &nh)
 {
-    if (nprob < 1 || !chains || !opts || !bytes || nstreams < 1 || nstreams > 64) return MBL_ERR_ARG;
-    int rc;
-    const size_t slot = batch_slot_bytes(nprob, chains, opts, &rc);
-    if (rc != MBL_OK) return rc;
-    *bytes = slot * (size_t)std::min(nstreams, nprob);
-    return MBL_OK;
-}
-
-extern "C" int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, const double *sigmas,
-                                        const mbl_lobpcg_opts *opts, const double *X0_dev, int nstreams,
-                                        void *workspace_dev, size_t workspace_bytes, double *evals_host,
-                                        double *evecs_dev, double *resid_host, mbl_lobpcg_stats *stats,
-                                        mbl_stream_t stream)
-{
-    if (nprob < 1 || !chains || !opts || !X0_dev || !workspace_dev || nstreams < 1 || nstreams > 64)
-        return MBL_ERR_ARG;
-    if ((uintptr_t)workspace_dev % kAlign) return MBL_ERR_ARG;
-    int rc;
-    const size_t slot = batch_slot_bytes(nprob, chains, opts, &rc);
-    if (rc != MBL_OK) return rc;
-    const int ns = std::min(nstreams, nprob);
-    if (workspace_bytes < slot * (size_t)ns) return MBL_ERR_WORKSPACE;
-    if (opts->use_graph == 0 && opts->timing) return MBL_ERR_ARG;
-    // packed offsets of each problem's start block and eigenvectors
-    std::vector<int64_t> off_x(nprob + 1, 0), off_v(nprob + 1, 0);
-    for (int i = 0; i < nprob; ++i) {
-        const int64_t n = mbl_basis_size(chains[i].L, chains[i].n_up);
-        if (n <= 0 || (sigmas == nullptr && chains[i].L < 2)) return MBL_ERR_ARG;
-        off_x[i + 1] = off_x[i] + n * opts->k;
-        off_v[i + 1] = off_v[i] + n * opts->nev;
-    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MBL_ERR_CUDA;
-    // the workers start after the caller's prior work on its stream
     cudaEvent_t start_ev;
     if (cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) != cudaSuccess) return MBL_ERR_CUDA;
-    if (cudaEventRecord(start_ev, (cudaStream_t)stream) != cudaSuccess) {
+    if (cudaEventRecord(start_ev, after) != cudaSuccess) {
         cudaEventDestroy(start_ev);
         return MBL_ERR_CUDA;
     }
     std::atomic<int> next{0};
     std::atomic<int> first_error{MBL_OK};
-    std::atomic<int> not_converged{0};
     auto worker = [&](int wid) {
         if (cudaSetDevice(dev) != cudaSuccess) {
             first_error.store(MBL_ERR_CUDA);
@@ -788,51 +804,373 @@ extern "C" int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, cons
             const int i = next.fetch_add(1);
             if (i >= nprob || first_error.load() != MBL_OK) break;
             const mbl_chain &ch = chains[i];
-            mbl_lobpcg_opts o = *opts;
-            double sigma = sigmas ? sigmas[i] : 0.0;
-            if (!sigmas) {
-                // sigma at the middle of the spectrum; ||H|| from the same bounds
-                double lo = 0.0, hi = 0.0;
-                int it = 0;
-                const double *xb = X0_dev + off_x[i];
-                ChainParams cpb;
-                int r1 = make_chain_params(&ch, 0.0, &cpb);
-                if (r1 == MBL_OK) r1 = ensure_lowtabs_for(ch.L);
-                if (r1 == MBL_OK)
-                    r1 = lanczos_bounds(cpb, mbl_basis_size(ch.L, ch.n_up), xb, opts->k, kBatchBoundsTol, 1000, ws,
-                                        slot, &lo, &hi, &it, st);
-                if (r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) {
-                    first_error.store(r1);
-                    break;
-                }
-                sigma = 0.5 * (lo + hi);
-                if (!(o.norm_h > 0.0)) o.norm_h = std::max(std::fabs(lo), std::fabs(hi));
-            }
-            mbl_lobpcg_stats stt{};
-            const int r = mbl_lobpcg_solve(&ch, sigma, &o, X0_dev + off_x[i], ws, slot,
-                                           evals_host ? evals_host + (size_t)i * o.nev : nullptr,
-                                           evecs_dev ? evecs_dev + off_v[i] : nullptr,
-                                           resid_host ? resid_host + (size_t)i * o.nev : nullptr, &stt,
-                                           (mbl_stream_t)st);
-            if (stats) stats[i] = stt;
-            if (r == MBL_ERR_NOT_CONVERGED) {
-                not_converged.fetch_add(1);
-            } else if (r != MBL_OK) {
+            double lo = 0.0, hi = 0.0;
+            int it = 0;
+            ChainParams cpb;
+            int r1 = make_chain_params(&ch, 0.0, &cpb);
+            if (r1 == MBL_OK) r1 = ensure_lowtabs_for(ch.L);
+            if (r1 == MBL_OK)
+                r1 = lanczos_bounds(cpb, mbl_basis_size(ch.L, ch.n_up), X0_dev + off_x[i], k, kBatchBoundsTol, 1000,
+                                    ws, slot, &lo, &hi, &it, st);
+            if (r1 != MBL_OK && r1 != MBL_ERR_NOT_CONVERGED) {
                 int expect = MBL_OK;
-                first_error.compare_exchange_strong(expect, r);
+                first_error.compare_exchange_strong(expect, r1);
                 break;
             }
+            sig[i] = 0.5 * (lo + hi);
+            nh[i] = norm_given > 0.0 ? norm_given : std::max(std::fabs(lo), std::fabs(hi));
         }
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     };
     std::vector<std::thread> pool;
-    pool.reserve(ns);
-    for (int w = 0; w < ns; ++w) pool.emplace_back(worker, w);
+    for (int w = 0; w < nth; ++w) pool.emplace_back(worker, w);
     for (auto &t : pool) t.join();
     cudaEventDestroy(start_ev);
-    if (first_error.load() != MBL_OK) return first_error.load();
-    return not_converged.load() ? MBL_ERR_NOT_CONVERGED : MBL_OK;
+    return first_error.load();
+}
+
+constexpr int kBatchSubStreams = 16;
+
+// The streams (and their join events) of a batched solve, released on scope exit.
+struct SubStreams {
+    cudaStream_t cap = nullptr;  // for capturing the lanes' graphs
+    cudaStream_t st[kBatchSubStreams] = {};
+    cudaEvent_t ev[kBatchSubStreams] = {};
+    cudaEvent_t ev_main = nullptr;
+    int count = 0;
+    int create(int n)
+    {
+        if (cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+            return MBL_ERR_CUDA;
+        for (; count < n; ++count)
+            if (cudaStreamCreateWithFlags(&st[count], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev[count], cudaEventDisableTiming) != cudaSuccess)
+                return MBL_ERR_CUDA;
+        return MBL_OK;
+    }
+    ~SubStreams()
+    {
+        for (int j = 0; j < kBatchSubStreams; ++j) {
+            if (st[j]) {
+                cudaStreamSynchronize(st[j]);
+                cudaStreamDestroy(st[j]);
+            }
+            if (ev[j]) cudaEventDestroy(ev[j]);
+        }
+        if (ev_main) cudaEventDestroy(ev_main);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+// The captured steps of one lane's problem: before the preconditioner, and after it
+// without / with the previous direction P (about 40 small kernels each, launched as one
+// graph per round), with the products each counts.
+struct LaneGraphs {
+    cudaGraphExec_t pre = nullptr, post[2] = {nullptr, nullptr};
+    int64_t kernels_pre = 0, kernels_post[2] = {0, 0};
+    int64_t matvecs_post[2] = {0, 0};
+    void reset()
+    {
+        if (pre) cudaGraphExecDestroy(pre);
+        for (auto &g : post)
+            if (g) cudaGraphExecDestroy(g);
+        pre = post[0] = post[1] = nullptr;
+        kernels_pre = kernels_post[0] = kernels_post[1] = 0;
+        matvecs_post[0] = matvecs_post[1] = 0;
+    }
+};
+
+// Capture what enqueue() puts on s.st into an executable graph (s.st is swapped for the
+// capture stream meanwhile); *kernels = its kernel nodes.
+template <typename F>
+int capture_graph(Solver &s, cudaStream_t cap, F enqueue, cudaGraphExec_t *exec, int64_t *kernels)
+{
+    cudaStream_t user = s.st;
+    s.st = cap;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        s.st = user;
+        return MBL_ERR_CUDA;
+    }
+    set_capturing(true);
+    const int rc = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+    set_capturing(false);
+    s.st = user;
+    if (rc != MBL_OK || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return rc != MBL_OK ? rc : MBL_ERR_CUDA;
+    }
+    size_t nn = 0;
+    *kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+            for (size_t i = 0; i < nn; ++i) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++*kernels;
+            }
+    }
+    const cudaError_t ie = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return ie == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+// One lane of the lock-step batch.
+struct Lane {
+    LaneGraphs graphs;
+    ~Lane() { graphs.reset(); }
+    Solver s;
+    int prob = -1;  // problem in the lane, -1: idle
+    int it = 0;
+    bool have_p = false;
+    bool body = false;  // advances this round
+    double r_mark = 0.0;
+    int it_mark = 0;
+    std::chrono::steady_clock::time_point t0;
+};
+
+}  // namespace
+
+extern "C" int mbl_batched_workspace_size(int nprob, const mbl_chain *chains, const mbl_lobpcg_opts *opts,
+                                          int nstreams, size_t *bytes)
+{
+    if (nprob < 1 || !chains || !opts || !bytes || nstreams < 1 || nstreams > 64) return MBL_ERR_ARG;
+    int rc;
+    const size_t slot = batch_slot_bytes(nprob, chains, opts, &rc);
+    if (rc != MBL_OK) return rc;
+    const int ns = std::min(nstreams, nprob);
+    *bytes = slot * (size_t)ns + batch_table_bytes(ns);
+    return MBL_OK;
+}
+
+extern "C" int mbl_lobpcg_solve_batched(int nprob, const mbl_chain *chains, const double *sigmas,
+                                        const mbl_lobpcg_opts *opts, const double *X0_dev, int nstreams,
+                                        void *workspace_dev, size_t workspace_bytes, double *evals_host,
+                                        double *evecs_dev, double *resid_host, mbl_lobpcg_stats *stats,
+                                        mbl_stream_t stream)
+{
+    if (nprob < 1 || !chains || !opts || !X0_dev || !workspace_dev || nstreams < 1 || nstreams > 64)
+        return MBL_ERR_ARG;
+    if ((uintptr_t)workspace_dev % kAlign) return MBL_ERR_ARG;
+    int rc;
+    const size_t slot = batch_slot_bytes(nprob, chains, opts, &rc);
+    if (rc != MBL_OK) return rc;
+    const int ns = std::min(nstreams, nprob);
+    if (workspace_bytes < slot * (size_t)ns + batch_table_bytes(ns)) return MBL_ERR_WORKSPACE;
+    if (opts->use_graph == 0 && opts->timing) return MBL_ERR_ARG;
+    // packed offsets of each problem's start block and eigenvectors
+    std::vector<int64_t> off_x(nprob + 1, 0), off_v(nprob + 1, 0);
+    for (int i = 0; i < nprob; ++i) {
+        const int64_t n = mbl_basis_size(chains[i].L, chains[i].n_up);
+        if (n <= 0 || (sigmas == nullptr && chains[i].L < 2)) return MBL_ERR_ARG;
+        off_x[i + 1] = off_x[i] + n * opts->k;
+        off_v[i + 1] = off_v[i] + n * opts->nev;
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    // shifts and tolerance norms
+    std::vector<double> sig(nprob), nh(nprob, opts->norm_h);
+    if (sigmas) {
+        for (int i = 0; i < nprob; ++i) sig[i] = sigmas[i];
+    } else {
+        MBL_TRY(batch_bounds(nprob, chains, X0_dev, off_x, opts->k, workspace_dev, slot, ns, st, opts->norm_h, sig, nh));
+    }
+    PcgLane *table_dev = reinterpret_cast<PcgLane *>((char *)workspace_dev + slot * (size_t)ns);
+    std::vector<PcgLane> table((size_t)ns);
+    std::vector<Lane> lanes((size_t)ns);
+    // the lanes' own steps run on nsub streams (lane l on stream l mod nsub), so that the
+    // small kernels of different lanes overlap on the GPU; events join them to `st` around
+    // the batched PCG launches and at the end of each round
+    const int nsub = std::min(ns, kBatchSubStreams);
+    SubStreams sub;
+    MBL_TRY(sub.create(nsub));
+    auto fork = [&]() -> int {  // the sub-streams wait for the work queued on st
+        if (cudaEventRecord(sub.ev_main, st) != cudaSuccess) return MBL_ERR_CUDA;
+        for (int j = 0; j < nsub; ++j)
+            if (cudaStreamWaitEvent(sub.st[j], sub.ev_main, 0) != cudaSuccess) return MBL_ERR_CUDA;
+        return MBL_OK;
+    };
+    auto join = [&]() -> int {  // st waits for the work queued on the sub-streams
+        for (int j = 0; j < nsub; ++j)
+            if (cudaEventRecord(sub.ev[j], sub.st[j]) != cudaSuccess || cudaStreamWaitEvent(st, sub.ev[j], 0) != cudaSuccess)
+                return MBL_ERR_CUDA;
+        return MBL_OK;
+    };
+    const int mixed = opts->mode == MBL_MODE_MIXED;
+    const int k = opts->k, nev = opts->nev;
+    const bool graphs = opts->use_graph != 0;
+    constexpr int kStallIters = 20;  // as in mbl_lobpcg_solve
+    int next = 0, not_converged = 0;
+
+    // put problem next (if any) into lane l: its setup is enqueued now, its first status
+    // is read in the next round
+    auto assign = [&](int l) -> int {
+        Lane &ln = lanes[(size_t)l];
+        ln.prob = -1;
+        if (next >= nprob) return MBL_OK;
+        const int i = next++;
+        mbl_lobpcg_opts o = *opts;
+        o.norm_h = nh[(size_t)i];
+        o.timing = 0;
+        ln.graphs.reset();
+        ln.s = Solver{};
+        ln.t0 = std::chrono::steady_clock::now();
+        MBL_TRY(solver_setup(ln.s, &chains[i], sig[(size_t)i], &o, mbl_basis_size(chains[i].L, chains[i].n_up),
+                             X0_dev + off_x[i], (char *)workspace_dev + slot * (size_t)l, slot, sub.st[l % nsub]));
+        ln.prob = i;
+        ln.it = 0;
+        ln.have_p = false;
+        ln.r_mark = 0.0;
+        ln.it_mark = 0;
+        return MBL_OK;
+    };
+    // results of lane l's problem (its status words say it is done); evecs by a kernel
+    auto finish = [&](int l, int status) -> int {
+        Lane &ln = lanes[(size_t)l];
+        Solver &s = ln.s;
+        const int i = ln.prob;
+        MBL_TRY(gather_cols(k, nev, s.b.V, s.b.iflags + 8, s.b.Csel, s.st));
+        if (evecs_dev)
+            MBL_TRY(update(s.X(), s.ld3(), k, s.b.Csel, nev, nev, nullptr, 0, evecs_dev + off_v[i], nev, s.n, 1.0, 0.0,
+                           0, s.st));
+        double mu_h[64], res_h[64];
+        int sel_h[64];
+        if (cudaMemcpy(mu_h, s.b.mu, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(sel_h, s.b.iflags + 8, sizeof(int) * nev, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(res_h, s.b.res_sel, sizeof(double) * nev, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MBL_ERR_CUDA;
+        double mx = 0.0;
+        for (int j = 0; j < nev; ++j) {
+            if (evals_host) evals_host[(size_t)i * nev + j] = sig[(size_t)i] + mu_h[sel_h[j]];
+            if (resid_host) resid_host[(size_t)i * nev + j] = res_h[j];
+            mx = std::fmax(mx, res_h[j] / s.norm_h);
+        }
+        if (stats) {
+            mbl_lobpcg_stats sv{};
+            sv.iters = ln.it;
+            sv.converged = status == MBL_OK ? 1 : 0;
+            sv.matvecs = s.matvecs;
+            sv.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - ln.t0).count();
+            sv.max_rel_resid = mx;
+            sv.norm_h = s.norm_h;
+            stats[i] = sv;
+        }
+        if (status == MBL_ERR_NOT_CONVERGED) ++not_converged;
+        return MBL_OK;
+    };
+
+    MBL_TRY(fork());
+    for (int l = 0; l < ns; ++l) MBL_TRY(assign(l));
+    MBL_TRY(join());
+    for (;;) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return MBL_ERR_CUDA;
+        MBL_TRY(fork());
+        int busy = 0;
+        for (int l = 0; l < ns; ++l) {
+            Lane &ln = lanes[(size_t)l];
+            ln.body = false;
+            if (ln.prob < 0) continue;
+            Solver &s = ln.s;
+            HostStatus hs;
+            if (cudaMemcpy(hs.iflags, s.b.iflags, sizeof(hs.iflags), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(hs.dstat, s.b.dstat, sizeof(hs.dstat), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return MBL_ERR_CUDA;
+            if (s.gmix) {  // the stall rule of mbl_lobpcg_solve
+                const double r = hs.dstat[0];
+                if (ln.it == 0 || r < 0.9 * ln.r_mark) {
+                    ln.r_mark = r;
+                    ln.it_mark = ln.it;
+                } else if (ln.it - ln.it_mark >= kStallIters) {
+                    s.gmix = 0;
+                    ln.graphs.reset();
+                }
+            }
+            if (hs.iflags[5] || hs.iflags[2]) return MBL_ERR_NUMERIC;
+            if (hs.iflags[0]) return MBL_ERR_BREAKDOWN;
+            const bool done = hs.iflags[4] != 0;
+            if (done || ln.it >= opts->max_iter) {
+                MBL_TRY(finish(l, done ? MBL_OK : MBL_ERR_NOT_CONVERGED));
+                MBL_TRY(assign(l));
+                if (ln.prob >= 0) ++busy;  // its first status comes next round
+                continue;
+            }
+            ln.body = true;
+            ++busy;
+        }
+        if (busy == 0) {
+            MBL_TRY(join());
+            break;
+        }
+        // one LOBPCG iteration of every advancing lane
+        int nb = 0;
+        for (int l = 0; l < ns; ++l) {
+            Lane &ln = lanes[(size_t)l];
+            if (!ln.body) continue;
+            ++nb;
+            if (!graphs) {
+                MBL_TRY(ln.s.enqueue_pre_pcg());
+                continue;
+            }
+            if (!ln.graphs.pre)
+                MBL_TRY(capture_graph(ln.s, sub.cap, [&]() { return ln.s.enqueue_pre_pcg(); }, &ln.graphs.pre,
+                                      &ln.graphs.kernels_pre));
+            if (cudaGraphLaunch(ln.graphs.pre, ln.s.st) != cudaSuccess) return MBL_ERR_CUDA;
+            note_launch(ln.graphs.kernels_pre);
+        }
+        MBL_TRY(join());
+        if (nb > 0 && opts->pcg_iters > 0) {
+            // the lanes' table for the batched PCG launches; widths or tile settings without a
+            // tiled kernel (pcg_lane_fill refuses them) run each lane's own PCG launches
+            uint32_t round0 = 0, row0 = 0;
+            int nt = 0, fill = MBL_OK;
+            for (int l = 0; l < ns && fill == MBL_OK; ++l) {
+                Lane &ln = lanes[(size_t)l];
+                if (!ln.body) continue;
+                Solver &s = ln.s;
+                fill = pcg_lane_fill(&table[(size_t)nt++], s.cp, (uint32_t)s.n, k, mixed, s.b.dinv, s.b.pr, s.b.pp,
+                                     s.b.pt, s.b.pw, s.pcg_dev(), &round0, &row0);
+            }
+            if (fill == MBL_ERR_ARG) {
+                MBL_TRY(fork());
+                for (int l = 0; l < ns; ++l)
+                    if (lanes[(size_t)l].body) MBL_TRY(lanes[(size_t)l].s.enqueue_pcg_steps());
+                MBL_TRY(join());
+            } else {
+                MBL_TRY(fill);
+                if (cudaMemcpyAsync(table_dev, table.data(), sizeof(PcgLane) * (size_t)nt, cudaMemcpyHostToDevice,
+                                    st) != cudaSuccess)
+                    return MBL_ERR_CUDA;
+                for (int step = 0; step < opts->pcg_iters; ++step)
+                    MBL_TRY(pcg_batch_step(mixed, table_dev, nt, k, round0, row0, st));
+            }
+        }
+        MBL_TRY(fork());
+        for (int l = 0; l < ns; ++l) {
+            Lane &ln = lanes[(size_t)l];
+            if (!ln.body) continue;
+            if (!graphs) {
+                MBL_TRY(ln.s.enqueue_post_pcg(ln.have_p));
+            } else {
+                const int g = ln.have_p ? 1 : 0;
+                if (!ln.graphs.post[g]) {
+                    const int64_t mv = ln.s.matvecs;
+                    MBL_TRY(capture_graph(ln.s, sub.cap, [&]() { return ln.s.enqueue_post_pcg(ln.have_p); },
+                                          &ln.graphs.post[g], &ln.graphs.kernels_post[g]));
+                    ln.graphs.matvecs_post[g] = ln.s.matvecs - mv;
+                    ln.s.matvecs = mv;
+                }
+                if (cudaGraphLaunch(ln.graphs.post[g], ln.s.st) != cudaSuccess) return MBL_ERR_CUDA;
+                note_launch(ln.graphs.kernels_post[g]);
+                ln.s.matvecs += ln.graphs.matvecs_post[g];
+            }
+            ln.have_p = true;
+            ++ln.it;
+        }
+        MBL_TRY(join());
+    }
+    return not_converged ? MBL_ERR_NOT_CONVERGED : MBL_OK;
 }
 
 extern "C" int64_t mbl_kernel_launch_count(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
