@@ -628,7 +628,8 @@ def run_profile(args):
     (k = 64) FP32 block products three times each; 'pcg' runs the bench solve for two
     LOBPCG iterations of 30 PCG steps each, graphs on (the kernels of a step, ~300 launches);
     'bounds' runs the spectrum bounds of the bench workload once; 'gram' runs the
-    tensor-core Gram at n = 184,756 (96 x 96) and n = 705,432 (192 x 192) twice each."""
+    tensor-core Gram at n = 184,756 (96 x 96) and n = 705,432 (192 x 192) twice each;
+    'batch' runs four lock-step rounds of the batched solve on 64 L = 16 problems."""
     import torch
     import paper_2012_00217_gb300 as mbl
     dev = torch.device("cuda:0")
@@ -657,6 +658,18 @@ def run_profile(args):
                 mbl.binding.gram(A, A, "f32", 2)
             torch.cuda.synchronize()
             del A
+    elif args.profile == "batch":
+        # the batched solve on 64 lanes: the first 64 disorder-averaging problems at W = 2
+        # (L = 16, open, k = 16, nev = 8, 240 PCG steps), four LOBPCG iterations, sigma = 0
+        k, nev, W = BATCH_SAMPLE["k"], BATCH_SAMPLE["nev"], 2.0
+        probs = wl.batched_problems(W)[:64]
+        chains = [mbl.make_chain(p["L"], wl.batched_fields(p["L"], W, p["seed"]), p["delta"], p["periodic"])
+                  for p in probs]
+        X0 = torch.cat([torch.from_numpy(wl.initial_block(wl.sector_dim(p["L"]), k, p["seed"])) for p in probs]).to(dev)
+        opts = mbl.make_opts(nev, k, tol=1e-8, max_iter=4, pcg_iters=BATCH_SAMPLE["pcg_iters"], mode=mbl.MODE_MIXED)
+        ws = torch.empty(mbl.binding.batched_workspace_size(chains, opts, 64), dtype=torch.uint8, device=dev)
+        mbl.binding.lobpcg_solve_batched(chains, opts, X0, ws, 64, sigmas=[0.0] * len(probs), allow_not_converged=True)
+        torch.cuda.synchronize()
     elif args.profile == "bounds":
         s = _setup(torch, mbl, dev)
         step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
@@ -690,7 +703,7 @@ def main():
                     help="time the CPU oracle only (product sweep and small whole solves) on this host")
     ap.add_argument("--cpu-sweep-L", default="22,24,26", help="chain lengths of the oracle product sweep")
     ap.add_argument("--cpu-sweep-no-solves", action="store_true", help="product sweep only")
-    ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram"], default=None,
+    ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram", "batch"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
                          "FP32), a short solve (2 iterations x 30 PCG steps), the spectrum bounds or the "
                          "tensor-core Grams, for an ncu capture")
