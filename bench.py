@@ -629,7 +629,8 @@ def run_profile(args):
     LOBPCG iterations of 30 PCG steps each, graphs on (the kernels of a step, ~300 launches);
     'bounds' runs the spectrum bounds of the bench workload once; 'gram' runs the
     tensor-core Gram at n = 184,756 (96 x 96) and n = 705,432 (192 x 192) twice each;
-    'batch' runs four lock-step rounds of the batched solve on 64 L = 16 problems."""
+    'batch' runs four lock-step rounds of the batched solve on 64 L = 16 problems; 'step'
+    runs one bench step (autotuned, after a warm-up step) inside the NVTX range "step"."""
     import torch
     import paper_2012_00217_gb300 as mbl
     dev = torch.device("cuda:0")
@@ -658,6 +659,18 @@ def run_profile(args):
                 mbl.binding.gram(A, A, "f32", 2)
             torch.cuda.synchronize()
             del A
+    elif args.profile == "step":
+        # one bench step exactly as timed (products autotuned first, one warm-up step), the
+        # timed step inside the NVTX range "step" for a launch list restricted to it
+        s = _setup(torch, mbl, dev)
+        autotune_step(torch, mbl, dev, s)
+        step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
+        step.run()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("step")
+        step.run()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     elif args.profile == "batch":
         # the batched solve on 64 lanes: the first 64 disorder-averaging problems at W = 2
         # (L = 16, open, k = 16, nev = 8, 240 PCG steps), four LOBPCG iterations, sigma = 0
@@ -703,7 +716,7 @@ def main():
                     help="time the CPU oracle only (product sweep and small whole solves) on this host")
     ap.add_argument("--cpu-sweep-L", default="22,24,26", help="chain lengths of the oracle product sweep")
     ap.add_argument("--cpu-sweep-no-solves", action="store_true", help="product sweep only")
-    ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram", "batch"], default=None,
+    ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram", "batch", "step"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
                          "FP32), a short solve (2 iterations x 30 PCG steps), the spectrum bounds or the "
                          "tensor-core Grams, for an ncu capture")

@@ -173,12 +173,14 @@ int mbl_autotune_product(const mbl_chain *chain, int dtype, const void *X_dev, v
                          int reps, mbl_product_choice *choice, mbl_stream_t stream);
 
 /* Tuning: engine of the FP32 Gram matrices of mixed mode (S^T S, S^T A S, X^T A X; the
- * tall-skinny contraction of the Rayleigh-Ritz step, Sec. 3.2): 0 = default (tensor cores
- * when both sides are >= 96, else CUDA cores), 1 = CUDA cores (FP32 FMA), 2 = tensor
- * cores whenever the shape fits (tcgen05.mma kind::tf32 with FP32
+ * tall-skinny contraction of the Rayleigh-Ritz step, Sec. 3.2) and of its FP32 block
+ * updates (the projections of W and P against X and the new direction P): 0 = default
+ * (tensor cores for Grams whose sides are both >= 96, CUDA cores otherwise), 1 = CUDA cores
+ * (FP32 FMA), 2 = tensor cores whenever the shape fits (tcgen05.mma kind::tf32 with FP32
  * accumulators in tensor memory; each FP32 operand split into two TF32 parts, three
- * products, error of the order of FP32 rounding; for Grams up to 256 x 256).  Applies to
- * later solves in this process.  Returns MBL_ERR_ARG for any other value. */
+ * products, error of the order of FP32 rounding; Grams up to 256 x 256, updates with
+ * p <= 192, q <= 64).  Applies to later solves in this process.  Returns MBL_ERR_ARG for
+ * any other value. */
 int mbl_set_gram_engine(int engine);
 
 /* The tall-skinny Gram of the Rayleigh-Ritz step (Sec. 3.2), on its own: C = A^T B for
@@ -193,6 +195,22 @@ int mbl_gram_workspace_size(int64_t n, int p, int q, size_t *bytes);
 int mbl_gram(const double *A_dev, int64_t lda, int p, const double *B_dev, int64_t ldb, int q, int64_t n,
              double *C_dev, int64_t ldc, int precision, int engine, void *workspace_dev, size_t workspace_bytes,
              mbl_stream_t stream);
+
+/* The block update of the LOBPCG step (Sec. 3.2: X <- S C, P <- [W P] C and the
+ * projections B - X (X^T B)) on its own: D = beta C + alpha A M for FP64 device blocks
+ * A (n x p, row-major, lda >= p), M (p x q, ldm >= q), C and D (n x q, ldc, ldd >= q; C may
+ * be D, or NULL when beta = 0), 1 <= p <= 192, 1 <= q <= 64.  precision MBL_F64: FP64
+ * arithmetic (CUDA cores); MBL_F32: inputs rounded to FP32 and FP32 arithmetic, so
+ * |D - exact| is of the order of 2^-21 (|alpha| |A| |M| + |beta C|) elementwise, on the
+ * engine given (0: the process-wide choice of mbl_set_gram_engine, 1: CUDA cores, which add
+ * beta C in FP64, 2: tensor cores -- A, C and D moved by TMA, tcgen05.mma kind::tf32 over
+ * 128-row tiles with the accumulator in tensor memory, each FP32 operand split into two
+ * TF32 parts, three products; it needs A, D (and C when beta != 0) 16-byte aligned with even
+ * leading dimensions and otherwise runs on the CUDA cores; 2 with MBL_F64 is MBL_ERR_ARG).
+ * Allocates nothing; deterministic for a given engine; runs on `stream`. */
+int mbl_update(const double *A_dev, int64_t lda, int p, const double *M_dev, int64_t ldm, int q,
+               const double *C_dev, int64_t ldc, double *D_dev, int64_t ldd, int64_t n, double alpha,
+               double beta, int precision, int engine, mbl_stream_t stream);
 
 /* ---- folded-spectrum LOBPCG (Sec. 3.2, Sec. 6.2) ---------------------------------- */
 

@@ -35,7 +35,7 @@ EXPORTED = ("mbl_status_string", "mbl_basis_size", "mbl_basis_build", "mbl_basis
             "mbl_lobpcg_solve_batched", "mbl_kernel_launch_count",
             "mbl_set_product_schedule", "mbl_autotune_product", "mbl_set_gram_engine",
             "mbl_gram_workspace_size", "mbl_gram", "mbl_product_tile_width", "mbl_gap_ratio",
-            "mbl_entanglement_workspace_size", "mbl_entanglement_entropy")
+            "mbl_entanglement_workspace_size", "mbl_entanglement_entropy", "mbl_update")
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -115,6 +115,8 @@ def lib():
     so.mbl_set_gram_engine.argtypes = [i32]
     so.mbl_gram_workspace_size.restype = i32
     so.mbl_gram_workspace_size.argtypes = [i64, i32, i32, ctypes.POINTER(sz)]
+    so.mbl_update.restype = i32
+    so.mbl_update.argtypes = [p, i64, i32, p, i64, i32, p, i64, p, i64, i64, f64, f64, i32, i32, p]
     so.mbl_gram.restype = i32
     so.mbl_gram.argtypes = [p, i64, i32, p, i64, i32, i64, p, i64, i32, i32, p, sz, p]
     so.mbl_autotune_product.restype = i32
@@ -275,6 +277,25 @@ def gram(A, B, precision="f32", engine=0):
                           int(n), _dev(C, torch.float64, "C"), int(q), prec, int(engine), _dev(ws, torch.uint8, "ws"),
                           ws.numel(), _stream_ptr(A)), "mbl_gram")
     return C
+
+
+def update(A, M, C=None, alpha=1.0, beta=0.0, precision="f32", engine=0):
+    """mbl_update: D = beta C + alpha A M for contiguous FP64 CUDA tensors A (n x p), M (p x q)
+    and optional C (n x q); returns D as a new n x q FP64 CUDA tensor."""
+    torch = _torch()
+    if A.dim() != 2 or M.dim() != 2 or A.shape[1] != M.shape[0] or not (A.is_contiguous() and M.is_contiguous()):
+        raise ValueError("A (n x p), M (p x q): contiguous")
+    n, p_ = A.shape
+    q = M.shape[1]
+    if C is not None and (C.shape != (n, q) or not C.is_contiguous()):
+        raise ValueError("C: contiguous n x q")
+    D = torch.empty((n, q), dtype=torch.float64, device=A.device)
+    prec = MBL_F32 if precision == "f32" else MBL_F64
+    _check(lib().mbl_update(_dev(A, torch.float64, "A"), int(p_), int(p_), _dev(M, torch.float64, "M"), int(q), int(q),
+                            _dev(C, torch.float64, "C") if C is not None else None, int(q),
+                            _dev(D, torch.float64, "D"), int(q), int(n), float(alpha), float(beta), prec, int(engine),
+                            _stream_ptr(A)), "mbl_update")
+    return D
 
 
 def autotune_product(chain, X, Y, reps=5):

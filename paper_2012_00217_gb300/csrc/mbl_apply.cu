@@ -2105,7 +2105,6 @@ __global__ void __launch_bounds__(kThreads, MBL_TILED_MIN_BLOCKS)
     __shared__ ChainParams s_cp;
     __shared__ int s_lane;
     __shared__ unsigned s_last;
-    __shared__ double s_tot[64];
     load_binom(sbin);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G;
     const int col = (lane % G) * V;

@@ -14,7 +14,8 @@ namespace mbl {
 int gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n, double *C,
          int64_t ldc, int sym, int compute_f32, double *part, cudaStream_t st);
 size_t gram_partial_doubles(int64_t n, int p, int q);
-// Engine of the FP32 Grams: 0 = default, 1 = CUDA cores, 2 = tensor cores (tcgen05).
+// Engine of the FP32 Grams and block updates: 0 = default, 1 = CUDA cores, 2 = tensor
+// cores (tcgen05).
 void set_gram_engine(int engine);
 void set_gram_engine_local(int engine);  // this thread's next Grams (0: use the switch)
 // Tensor-core slab partials (mbl_gram_tc.cu): part[slab][i][j] for nslab slabs.
@@ -22,6 +23,13 @@ bool gram_tc_supported(int p, int q);
 int gram_tc_slabs(int64_t n, int p);
 int gram_tc_partial(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n, int nslab,
                     double *part, cudaStream_t st);
+// Tensor-core block update D = beta C + alpha A M with FP32 accuracy (mbl_gram_tc.cu):
+// p <= 192, q <= 64, A, D (and C when beta != 0) 16-byte aligned with even leading
+// dimensions (they are read and written by TMA).
+bool update_tc_supported(const double *A, int64_t lda, int p, int q, const double *C, int64_t ldc, const double *D,
+                         int64_t ldd, double beta);
+int update_tc(const double *A, int64_t lda, int p, const double *M, int64_t ldm, int q, const double *C, int64_t ldc,
+              double *D, int64_t ldd, int64_t n, double alpha, double beta, cudaStream_t st);
 
 // D = beta C + alpha A M  (A: n x p, M: p x q, C, D: n x q); D may alias C.
 int update(const double *A, int64_t lda, int p, const double *M, int64_t ldm, int q, const double *C, int64_t ldc,

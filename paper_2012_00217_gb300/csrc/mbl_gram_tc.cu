@@ -15,6 +15,7 @@
 // 16-byte core matrices, 128 B apart along K, 1024 B apart along M/N); one thread issues
 // the MMAs of a chunk and commits them to the buffer's mbarrier, which the next use of
 // that buffer waits on, so staging of chunk i+1 overlaps the MMAs of chunk i.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mbar_init(&s_mbar[0], 1);
         mbar_init(&s_mbar[1], 1);
     }
+    __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
                      "r"(tmem_cols)
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int i = 0; i < nchunks; ++i) {
         const int b = i & 1;
         if (i >= 2) ok = ok && mbar_wait(&s_mbar[b], (unsigned)(((i - 2) >> 1) & 1));
+        __syncwarp();
         if (!__syncthreads_and(ok)) break;
         unsigned char *base = tc_raw + b * buf_bytes;
         float *ahi = reinterpret_cast<float *>(base), *alo = reinterpret_cast<float *>(base + a_bytes);
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             mma_commit(&s_mbar[b]);
         }
+        __syncwarp();
     }
     // the last commit covers every MMA of the block
     if (nchunks > 0) {
@@ -190,6 +194,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ok = ok && done;
         if (!done && nchunks > 1) mbar_wait(&s_mbar[(last - 1) & 1], (unsigned)(((last - 1) >> 1) & 1));
     }
+    __syncwarp();
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // accumulator -> slab partial: warp w reads TMEM lanes 32 (w % 4) .. +31 and every
@@ -222,6 +227,526 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// ---------------------------------------------------------------------------------
+// Block update D = beta C + alpha A M (A: n x p, M: p x q, C, D: n x q, all FP64 in memory) of
+// the LOBPCG step (Sec. 3.2) with FP32 accuracy on the tensor cores: A and M rounded to FP32
+// and split into two TF32 parts as in the Gram above, D_acc = Ahi Mhi + Ahi Mlo + Alo Mhi per
+// k-step.  Here M of the MMA is a tile of 128 rows of A, N = q (padded to 16), K = p (padded
+// to 16).
+//
+// The kernel is HBM-bound (p + 2q doubles per row against ~6 p q tensor-core flops), so every
+// byte moves by TMA and the arithmetic is spread over warp roles of one persistent CTA per SM:
+//   warp 24      A producer: cp.async.bulk.tensor loads of 128-row x 16-column FP64 boxes of A
+//                (128-byte swizzle) into a ring of kUpdMaxStages-at-most 16 KB slots,
+//   warps 8-23   converters: FP64 -> hi/lo TF32 (bit operations, not the FP64 pipe) in the
+//                no-swizzle K-major core-matrix layout of the MMA, into a ring of (up to four)
+//                operand buffers, deep enough to cover the MMA-to-commit round trip,
+//   warp 25      MMA issuer (one thread): two k-steps of three kind::tf32 MMAs per box into
+//                one of two tensor-memory accumulators,
+//   warp 26      C producer: the tile's C (q/16 boxes) into one of one or two C/D slots,
+//   warps 0-7    epilogue: tcgen05.ld of the accumulator (warp w reads lanes 32 (w % 4) .. +31,
+//                thread = row, w / 4 picks alternate 16-column groups), D = beta C + alpha acc
+//                in FP32 (C rounded to FP32 like the other inputs; FP64 arithmetic here would be
+//                bound by GB300's narrow FP64 pipe), widened in place in the slot, then
+//                cp.async.bulk.tensor stores of the D tile.
+// Each ring and mbarrier has one waiting role that waits on every phase in turn (a parity
+// wait cannot tell phase u from u - 2).  M (both TF32 parts) is staged once per CTA.  Every
+// wait is bounded; on a timeout the CTA stops, waits (bounded) for its own copies and MMAs,
+// writes NaN into its tiles of D (the solver's finiteness check reports it) and returns.
+constexpr int kUpdMaxP = 192, kUpdMaxQ = 64;
+constexpr int kUpdThreads = 864;       // 27 warps
+constexpr int kUpdEpiThreads = 256;    // warps 0-7
+constexpr int kUpdConvThreads = 512;   // warps 8-23
+constexpr int kUpdOpBufs = 4;          // at most this many [hi, lo] operand buffers between converters and MMA
+constexpr int kUpdBoxBytes = 16384;    // 128 rows x 16 FP64 columns, one ring slot
+constexpr int kUpdKC = 16;             // K columns per ring slot
+constexpr int kUpdOpBytes = 8192;      // one TF32 operand part of a slot: 128 rows x 16 K
+constexpr int kUpdMaxStages = 8;
+constexpr int kUpdSmemMax = 230400;    // dynamic shared memory asked for (227 KB less the static part)
+
+struct UpdBars {
+    uint64_t full[kUpdMaxStages], empty[kUpdMaxStages];
+    uint64_t afull[kUpdOpBufs], aempty[kUpdOpBufs], accfull[2], accempty[2], cfull[2], cempty[2], done;
+};
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t *m)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(m)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *m, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(m)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_box(const CUtensorMap *map, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     (uint64_t)map),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+// AND of v over the 256 epilogue threads (named barrier 1): their branches stay uniform, so
+// the named barrier below never waits for a thread that has left
+__device__ __forceinline__ bool epi_all(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, 1, 256, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+// FP64 <-> FP32 without the FP64 pipe (a few integer ops per element on GB300, where F2F
+// runs on the narrow FP64 unit).
+// x = hi + lo in TF32 parts for the MMA, from the FP64 bits: x32 = x with its mantissa cut to
+// the top 23 bits (truncation: relative error below 2^-23), hi = x32 with its low 13 mantissa
+// bits cleared (a TF32 value), lo = tf32(x32 - hi) (x32 - hi is exact).  Four elements at a
+// time, branch-free on the common path; the rare operand outside the normal FP32 range goes
+// through the conversion instruction after one warp vote.
+__device__ __forceinline__ void split_tf32x4(const double (&x)[4], float (&h)[4], float (&l)[4])
+{
+    uint32_t u[4];
+    bool odd = false;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(x[e]);
+        const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
+        const uint32_t ex = (hi >> 20) & 0x7FFu;
+        const bool normal = ex - 897u <= 253u;  // FP32-normal range
+        u[e] = normal ? ((hi & 0x80000000u) | ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29))
+                      : (hi & 0x80000000u);  // zero and FP64 subnormals: signed zero
+        odd |= !normal && ex != 0u;
+    }
+    if (__any_sync(0xffffffffu, odd)) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t ex = (uint32_t)((unsigned long long)__double_as_longlong(x[e]) >> 52) & 0x7FFu;
+            if (ex - 897u > 253u && ex != 0u) u[e] = __float_as_uint((float)x[e]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        h[e] = __uint_as_float(u[e] & 0xFFFFE000u);
+        l[e] = to_tf32(__uint_as_float(u[e]) - h[e]);
+    }
+}
+
+// x cut to FP32 by its bits (top 23 mantissa bits); zero and FP64 subnormals give a signed
+// zero, values outside the normal FP32 range take the conversion instruction
+__device__ __forceinline__ float narrow_f32(double x)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
+    const uint32_t ex = (hi >> 20) & 0x7FFu;
+    if (ex - 897u <= 253u)
+        return __uint_as_float((hi & 0x80000000u) | ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+    if (ex == 0u) return __uint_as_float(hi & 0x80000000u);
+    return (float)x;
+}
+
+// widening is exact: the FP32 fields moved into FP64 position
+__device__ __forceinline__ double f32_to_f64_fast(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xFFu;
+    if (ex - 1u <= 253u)
+        return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)),
+                                (int)(u << 29));
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+}
+
+// byte offset of the 16-byte unit `unit` (FP64 columns 2 unit, 2 unit + 1) of row r inside
+// one 128-byte-swizzled box
+__device__ __forceinline__ uint32_t swz_off(int r, int unit) { return (uint32_t)(r * 128 + ((unit ^ (r & 7)) << 4)); }
+
+// operand part of one 16-wide K slot: 8-row x 16-byte core matrices, 128 B apart along K and
+// 512 B apart along the rows
+__device__ __forceinline__ uint32_t tile16_offset(int r, int kq) { return (uint32_t)((r >> 3) * 512 + kq * 128 + (r & 7) * 16); }
+
+__device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t addr, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// 16 accumulator columns of this thread's TMEM lane; the wait names the registers so no use
+// of them is scheduled before the load has landed
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                   "+r"(v[15])
+                 :
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kUpdThreads, 1)
+    k_update_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
+                 const __grid_constant__ CUtensorMap tmD, const double *__restrict__ M, int64_t ldm, int p, int q,
+                 int np, double *D, int64_t ldd, int64_t n, double alpha, double beta, int nstages, int ncs,
+                 int nab, uint32_t acc_cols)
+{
+    extern __shared__ unsigned char upd_raw[];
+    __shared__ __align__(8) UpdBars bars;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_err;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nck = (p + kUpdKC - 1) / kUpdKC;  // 16-wide K slots of A per tile
+    const int nm = (p + kTcKC - 1) / kTcKC;     // 32-wide K chunks of the staged M
+    const int ncb = (q + 15) / 16;              // 16-column boxes of C / D per tile
+    const uint32_t b_bytes = tile_bytes(np);
+    // 1024-byte aligned carve-up: A ring | ncs C/D slots | two [hi, lo] operand buffers | [hi, lo] x nm of M
+    const uint32_t raw0 = saddr(upd_raw);
+    const uint32_t pad = ((raw0 + 1023u) & ~1023u) - raw0;
+    unsigned char *ring = upd_raw + pad;
+    unsigned char *cslot = ring + (size_t)nstages * kUpdBoxBytes;
+    unsigned char *abuf = cslot + (size_t)ncs * ncb * kUpdBoxBytes;
+    unsigned char *mbuf = abuf + (size_t)2 * nab * kUpdOpBytes;
+    const int64_t ntiles = (n + kTcM - 1) / kTcM;
+    const int my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const bool use_c = beta != 0.0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nstages; ++s) {
+            mbar_init(&bars.full[s], 1);
+            mbar_init(&bars.empty[s], kUpdConvThreads);
+        }
+        for (int b = 0; b < nab; ++b) {
+            mbar_init(&bars.afull[b], kUpdConvThreads);
+            mbar_init(&bars.aempty[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars.accfull[b], 1);
+            mbar_init(&bars.accempty[b], kUpdEpiThreads);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars.cfull[b], 1);
+            mbar_init(&bars.cempty[b], 1);
+        }
+        mbar_init(&bars.done, 1);
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 25) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                     "r"(2 * acc_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // M^T as the B operand: row nn of the tile = column nn of M, K = rows of M (32 per chunk)
+    for (int task = threadIdx.x; task < nm * np * (kTcKC / 4); task += kUpdThreads) {
+        const int c = task / (np * (kTcKC / 4)), rem = task % (np * (kTcKC / 4));
+        const int nn = rem % np, kq = rem / np;
+        float h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kk = c * kTcKC + 4 * kq + i;
+            const float x = (kk < p && nn < q) ? (float)M[(int64_t)kk * ldm + nn] : 0.0f;
+            h[i] = to_tf32(x);
+            l[i] = to_tf32(x - h[i]);
+        }
+        const uint32_t off = tile_offset(nn, kq) / 4;
+        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(mbuf + (size_t)(2 * c) * b_bytes) + off) =
+            make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(mbuf + (size_t)(2 * c + 1) * b_bytes) + off) =
+            make_float4(l[0], l[1], l[2], l[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const int total = my_tiles * nck;  // ring positions of this CTA: tile i, slot c -> i nck + c
+
+    if (warp == 24) {
+        // ---------------- A producer ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (; issued < total && !s_err; ++issued) {
+                const int s = issued % nstages, u = issued / nstages;
+                if (u >= 1 && !mbar_wait(&bars.empty[s], (unsigned)((u - 1) & 1))) {
+                    s_err = 1;
+                    break;
+                }
+                const int i = issued / nck, c = issued % nck;
+                const int y = (int)((blockIdx.x + (int64_t)i * gridDim.x) * kTcM);
+                mbar_expect(&bars.full[s], (unsigned)kUpdBoxBytes);
+                tma_load_box(saddr(ring + (size_t)s * kUpdBoxBytes), &tmA, c * kUpdKC, y, &bars.full[s]);
+            }
+            // no copy may still be landing in shared memory when the CTA ends
+            for (int pos = issued > nstages ? issued - nstages : 0; pos < issued; ++pos)
+                if (!mbar_wait(&bars.full[pos % nstages], (unsigned)((pos / nstages) & 1))) s_err = 1;
+        }
+        __syncwarp();
+    } else if (warp == 26) {
+        // ---------------- C producer: tile i's C into C/D slot i % ncs ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (; issued < my_tiles && !s_err; ++issued) {
+                const int cs = issued % ncs, uc = issued / ncs;
+                if (uc >= 1 && !mbar_wait(&bars.cempty[cs], (unsigned)((uc - 1) & 1))) {
+                    s_err = 1;
+                    break;
+                }
+                if (!use_c) {
+                    mbar_arrive1(&bars.cfull[cs]);
+                    continue;
+                }
+                const int y = (int)((blockIdx.x + (int64_t)issued * gridDim.x) * kTcM);
+                unsigned char *dst = cslot + (size_t)cs * ncb * kUpdBoxBytes;
+                mbar_expect(&bars.cfull[cs], (unsigned)(ncb * kUpdBoxBytes));
+                for (int bx = 0; bx < ncb; ++bx)
+                    tma_load_box(saddr(dst + (size_t)bx * kUpdBoxBytes), &tmC, 16 * bx, y, &bars.cfull[cs]);
+            }
+            for (int t = issued > ncs ? issued - ncs : 0; t < issued; ++t)
+                if (!mbar_wait(&bars.cfull[t % ncs], (unsigned)((t / ncs) & 1))) s_err = 1;
+        }
+        __syncwarp();
+    } else if (warp == 25) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc_tf32(np);
+            for (int i = 0; i < my_tiles && !s_err; ++i) {
+                const int a = i & 1, ua = i >> 1;
+                if (ua >= 1 && !mbar_wait(&bars.accempty[a], (unsigned)((ua - 1) & 1))) {
+                    s_err = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d_tmem = tmem + (uint32_t)a * acc_cols;
+                bool bad = false;
+                for (int c = 0; c < nck; ++c) {
+                    const int g = i * nck + c, b = g % nab, ub = g / nab;
+                    if (!mbar_wait(&bars.afull[b], (unsigned)(ub & 1))) {
+                        bad = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = saddr(abuf + (size_t)(2 * b) * kUpdOpBytes), a1 = a0 + kUpdOpBytes;
+                    const uint32_t b0 = saddr(mbuf + (size_t)(2 * (c >> 1)) * b_bytes) + (uint32_t)(c & 1) * 512u;
+                    const uint32_t b1 = b0 + b_bytes;
+#pragma unroll
+                    for (int s2 = 0; s2 < kUpdKC / 8; ++s2) {
+                        const uint32_t ks = (uint32_t)s2 * 256u;
+                        const uint64_t dA0 = smem_desc_sbo(a0 + ks, 512u), dA1 = smem_desc_sbo(a1 + ks, 512u);
+                        const uint64_t dB0 = smem_desc_sbo(b0 + ks, 1024u), dB1 = smem_desc_sbo(b1 + ks, 1024u);
+                        mma_tf32(d_tmem, dA0, dB0, idesc, (c > 0 || s2 > 0) ? 1 : 0);
+                        mma_tf32(d_tmem, dA0, dB1, idesc, 1);
+                        mma_tf32(d_tmem, dA1, dB0, idesc, 1);
+                    }
+                    mma_commit(&bars.aempty[b]);
+                }
+                if (bad) {
+                    s_err = 1;
+                    break;
+                }
+                mma_commit(&bars.accfull[a]);
+            }
+            // every MMA of this CTA has completed before the tensor memory is released
+            mma_commit(&bars.done);
+            if (!mbar_wait(&bars.done, 0u)) s_err = 1;
+        }
+        __syncwarp();
+    } else if (warp >= 8) {
+        // ---------------- converters: 512 threads, warp cw owns rows 8 cw .. 8 cw + 7 ----------------
+        const int cw = warp - 8;
+        const int kq = lane >> 3;  // 4-column quad of the 16-column slot
+        for (int g = 0; g < total && !s_err; ++g) {
+            const int s = g % nstages, u = g / nstages;
+            const int b = g % nab, ub = g / nab;
+            if (!mbar_wait(&bars.full[s], (unsigned)(u & 1)) ||
+                (ub >= 1 && !mbar_wait(&bars.aempty[b], (unsigned)((ub - 1) & 1)))) {
+                s_err = 1;
+                break;
+            }
+            const unsigned char *slot = ring + (size_t)s * kUpdBoxBytes;
+            float *ahi = reinterpret_cast<float *>(abuf + (size_t)(2 * b) * kUpdOpBytes);
+            float *alo = reinterpret_cast<float *>(abuf + (size_t)(2 * b + 1) * kUpdOpBytes);
+            {
+                const int r = 8 * cw + (lane & 7);
+                // columns past p and rows past n were zero-filled by the copy
+                const double2 v0 = *reinterpret_cast<const double2 *>(slot + swz_off(r, 2 * kq));
+                const double2 v1 = *reinterpret_cast<const double2 *>(slot + swz_off(r, 2 * kq + 1));
+                const double x[4] = {v0.x, v0.y, v1.x, v1.y};
+                float h[4], l[4];
+                split_tf32x4(x, h, l);
+                const uint32_t off = tile16_offset(r, kq) / 4;
+                *reinterpret_cast<float4 *>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4 *>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+            mbar_arrive1(&bars.empty[s]);  // this thread's reads of the slot are done
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive1(&bars.afull[b]);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: 256 threads, thread = row of the tile x column half ----------------
+        const int quad = warp & 3, half = warp >> 2;
+        const int r = 32 * quad + lane;
+        const float alpha32 = (float)alpha, beta32 = (float)beta;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int a = i & 1, ua = i >> 1;
+            const int y = (int)((blockIdx.x + (int64_t)i * gridDim.x) * kTcM);
+            const int cs = i % ncs, uc = i / ncs;
+            unsigned char *tslot = cslot + (size_t)cs * ncb * kUpdBoxBytes;
+            bool ok = !s_err && mbar_wait(&bars.accfull[a], (unsigned)(ua & 1));
+            ok = ok && mbar_wait(&bars.cfull[cs], (unsigned)(uc & 1));
+            __syncwarp();
+            if (!epi_all(ok)) {
+                s_err = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int g16 = half; g16 * 16 < np; g16 += 2) {
+                uint32_t v[16];
+                tmem_ld16(tmem + (uint32_t)a * acc_cols + ((uint32_t)(32 * quad) << 16) + (uint32_t)(16 * g16), v);
+                unsigned char *bx = tslot + (size_t)g16 * kUpdBoxBytes;
+#pragma unroll
+                for (int uu = 0; uu < 8; ++uu) {
+                    double2 *cell = reinterpret_cast<double2 *>(bx + swz_off(r, uu));
+                    float d0 = alpha32 * __uint_as_float(v[2 * uu]), d1 = alpha32 * __uint_as_float(v[2 * uu + 1]);
+                    if (use_c) {
+                        const double2 cv = *cell;
+                        d0 = fmaf(beta32, narrow_f32(cv.x), d0);
+                        d1 = fmaf(beta32, narrow_f32(cv.y), d1);
+                    }
+                    *cell = make_double2(f32_to_f64_fast(d0), f32_to_f64_fast(d1));
+                }
+            }
+            // the accumulator may be overwritten by the tile after next
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive1(&bars.accempty[a]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (threadIdx.x == 0) {
+                for (int bxi = 0; bxi < ncb; ++bxi)
+                    tma_store_box(&tmD, 16 * bxi, y, saddr(tslot + (size_t)bxi * kUpdBoxBytes));
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                // a slot is handed back once its store has read it: with two slots the previous
+                // tile's store, with one this tile's
+                if (ncs == 2) {
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    if (i >= 1) mbar_arrive1(&bars.cempty[(i - 1) % 2]);
+                } else {
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    mbar_arrive1(&bars.cempty[0]);
+                }
+            }
+            __syncwarp();
+        }
+        if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_err) {
+        for (int i = 0; i < my_tiles; ++i) {
+            const int64_t r0 = (blockIdx.x + (int64_t)i * gridDim.x) * kTcM;
+            for (int e = threadIdx.x; e < kTcM * q; e += kUpdThreads) {
+                const int64_t row = r0 + e / q;
+                if (row < n) D[row * ldd + e % q] = (double)NAN;
+            }
+        }
+    }
+    __syncwarp();
+    if (warp == 25)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * acc_cols)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------------------------
+// Host side of the tensor maps: the driver's encoder, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder()
+{
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr) !=
+                cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// An FP64 row-major matrix (rows x cols, leading dimension ld) as a 2-D tensor map with
+// 16-column x 128-row boxes and 128-byte swizzle.
+bool fp64_box_map(CUtensorMap *m, const double *base, int64_t rows, int cols, int64_t ld)
+{
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(double)};
+    const cuuint32_t box[2] = {16, (cuuint32_t)kTcM};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tma_addressable(const double *base, int64_t ld) { return base && ((uintptr_t)base & 15u) == 0 && (ld & 1) == 0; }
+
+// shared memory of everything but the A ring, with ncs C/D slots and nab operand buffers
+size_t update_fixed_smem(int p, int q, int ncs, int nab)
+{
+    const int np = (q + 15) / 16 * 16, nm = (p + kTcKC - 1) / kTcKC;
+    return 1024 + (size_t)ncs * ((q + 15) / 16) * kUpdBoxBytes + (size_t)2 * nab * kUpdOpBytes +
+           (size_t)2 * nm * tile_bytes(np);
+}
+
+struct UpdConfig {
+    int ncs, nab, ns;  // C/D slots, operand buffers, A ring slots (0: does not fit)
+};
+
+// the deepest buffering that fits: two C/D slots and four operand buffers with an A ring of
+// at least four slots, else one C/D slot, else two operand buffers (an A ring of two slots
+// already keeps the loads ahead; the operand buffers cover the MMA round trip)
+UpdConfig update_config(int p, int q)
+{
+    const int cfg[3][3] = {{2, 4, 4}, {1, 4, 2}, {1, 2, 2}};
+    for (const auto &c : cfg) {
+        const size_t fixed = update_fixed_smem(p, q, c[0], c[1]);
+        if (fixed >= (size_t)kUpdSmemMax) continue;
+        int ns = (int)(((size_t)kUpdSmemMax - fixed) / kUpdBoxBytes);
+        if (ns > kUpdMaxStages) ns = kUpdMaxStages;
+        if (ns >= c[2]) return UpdConfig{c[0], c[1], ns};
+    }
+    return UpdConfig{1, 2, 0};
+}
+
 }  // namespace
 
 bool gram_tc_supported(int p, int q) { return p >= 1 && q >= 1 && p <= 256 && q <= 256; }
@@ -252,6 +777,43 @@ int gram_tc_partial(const double *A, int64_t lda, int p, const double *B, int64_
     dim3 grid((p + kTcM - 1) / kTcM, nslab);
     note_launch();
     k_gram_tc<<<grid, kTcThreads, smem, st>>>(A, lda, p, B, ldb, q, np, n, rps, part, tmem_cols);
+    return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
+}
+
+
+bool update_tc_supported(const double *A, int64_t lda, int p, int q, const double *C, int64_t ldc, const double *D,
+                         int64_t ldd, double beta)
+{
+    if (p < 1 || q < 1 || p > kUpdMaxP || q > kUpdMaxQ || update_config(p, q).ns < 2) return false;
+    if (!tensor_map_encoder()) return false;
+    return tma_addressable(A, lda) && tma_addressable(D, ldd) && (beta == 0.0 || tma_addressable(C, ldc));
+}
+
+int update_tc(const double *A, int64_t lda, int p, const double *M, int64_t ldm, int q, const double *C, int64_t ldc,
+              double *D, int64_t ldd, int64_t n, double alpha, double beta, cudaStream_t st)
+{
+    if (!update_tc_supported(A, lda, p, q, C, ldc, D, ldd, beta) || n > ((int64_t)1 << 31)) return MBL_ERR_ARG;
+    if (n <= 0) return MBL_OK;
+    const bool use_c = beta != 0.0;
+    CUtensorMap ta, tc, td;
+    if (!fp64_box_map(&ta, A, n, p, lda) || !fp64_box_map(&td, D, n, q, ldd) ||
+        !fp64_box_map(&tc, use_c ? C : D, n, q, use_c ? ldc : ldd))
+        return MBL_ERR_ARG;
+    const int np = (q + 15) / 16 * 16;
+    const uint32_t acc_cols = np <= 32 ? 32u : 64u;
+    const UpdConfig cfg = update_config(p, q);
+    const size_t smem = update_fixed_smem(p, q, cfg.ncs, cfg.nab) + (size_t)cfg.ns * kUpdBoxBytes;
+    static const bool attr = []() {
+        cudaFuncSetAttribute(k_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpdSmemMax);
+        return true;
+    }();
+    (void)attr;
+    const int64_t ntiles = (n + kTcM - 1) / kTcM;
+    int grid = num_sms();
+    if (grid > ntiles) grid = (int)ntiles;
+    note_launch();
+    k_update_tma<<<grid, kUpdThreads, smem, st>>>(ta, tc, td, M, ldm, p, q, np, D, ldd, n, alpha, beta, cfg.ns,
+                                                   cfg.ncs, cfg.nab, acc_cols);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
 

@@ -1206,3 +1206,21 @@ extern "C" int mbl_gram(const double *A_dev, int64_t lda, int p, const double *B
     mbl::set_gram_engine_local(0);
     return rc;
 }
+
+extern "C" int mbl_update(const double *A_dev, int64_t lda, int p, const double *M_dev, int64_t ldm, int q,
+                          const double *C_dev, int64_t ldc, double *D_dev, int64_t ldd, int64_t n, double alpha,
+                          double beta, int precision, int engine, mbl_stream_t stream)
+{
+    if (!A_dev || !M_dev || !D_dev || n < 0 || n > ((int64_t)1 << 31) || p < 1 || q < 1 || p > 192 || q > 64)
+        return MBL_ERR_ARG;
+    if (lda < p || ldm < q || ldd < q || (C_dev && ldc < q) || (!C_dev && beta != 0.0)) return MBL_ERR_ARG;
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return MBL_ERR_ARG;
+    if ((precision != MBL_F32 && precision != MBL_F64) || engine < 0 || engine > 2) return MBL_ERR_ARG;
+    if (precision == MBL_F64 && engine == 2) return MBL_ERR_ARG;  // the tensor-core path is FP32-accurate
+    const int f32 = precision == MBL_F32;
+    mbl::set_gram_engine_local(f32 ? engine : 1);
+    const int rc = mbl::update(A_dev, lda, p, M_dev, ldm, q, C_dev, C_dev ? ldc : 0, D_dev, ldd, n, alpha, beta, f32,
+                               (cudaStream_t)stream);
+    mbl::set_gram_engine_local(0);
+    return rc;
+}

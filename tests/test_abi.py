@@ -286,6 +286,30 @@ def test_gap_ratio_checks_arguments_before_any_launch(so):
         assert so.mbl_gap_ratio(nprob, m, ptrs[0], ld, ptrs[1], ptrs[2], None) == want
 
 
+def test_update_checks_arguments_before_any_launch(so):
+    """mbl_update refuses bad shapes, leading dimensions, precision/engine pairs and a
+    missing C with beta != 0 on the host; n = 0 launches nothing."""
+    from paper_2012_00217_gb300 import binding
+    ok, bad = binding.MBL_OK, binding.MBL_ERR_ARG
+    f = ctypes.c_void_p(1 << 20)  # never dereferenced: every case fails its checks or launches nothing
+    F32, F64 = binding.MBL_F32, binding.MBL_F64
+    cases = (  # A, lda, p, M, ldm, q, C, ldc, D, ldd, n, alpha, beta, precision, engine, want
+        (f, 8, 8, f, 8, 8, f, 8, f, 8, 0, 1.0, 1.0, F32, 2, ok),
+        (f, 8, 8, f, 8, 8, f, 8, f, 8, 0, 1.0, 1.0, F64, 2, bad),
+        (f, 193, 193, f, 8, 8, f, 8, f, 8, 10, 1.0, 0.0, F32, 2, bad),
+        (f, 8, 8, f, 65, 65, f, 65, f, 65, 10, 1.0, 0.0, F32, 2, bad),
+        (f, 7, 8, f, 8, 8, f, 8, f, 8, 10, 1.0, 0.0, F32, 1, bad),
+        (f, 8, 8, f, 8, 8, None, 8, f, 8, 10, 1.0, 0.5, F32, 1, bad),
+        (f, 8, 8, f, 8, 8, f, 8, f, 8, 10, float("nan"), 0.0, F32, 1, bad),
+        (f, 8, 8, f, 8, 8, f, 8, f, 8, 10, 1.0, 0.0, 3, 1, bad),
+        (f, 8, 8, f, 8, 8, f, 8, f, 8, 10, 1.0, 0.0, F32, 3, bad),
+        (None, 8, 8, f, 8, 8, f, 8, f, 8, 10, 1.0, 0.0, F32, 1, bad),
+        (f, 8, 8, f, 8, 8, f, 8, f, 8, -1, 1.0, 0.0, F32, 1, bad),
+    )
+    for *args, want in cases:
+        assert so.mbl_update(*args, None) == want, args
+
+
 def test_entanglement_workspace_and_argument_checks(so):
     import paper_2012_00217_gb300 as mbl
     from paper_2012_00217_gb300 import binding

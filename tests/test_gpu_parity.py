@@ -403,3 +403,78 @@ def test_gram_engines_match_fp64(mbl, n, p, q, engine):
         assert (err / scale).max() < 2.0 ** -18
     C64 = mbl.binding.gram(_gpu(A), _gpu(B), "f64", 1).cpu().numpy()
     assert np.abs(C64 - ref).max() <= 1e-12 * scale.max()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,p,q", [(1000, 8, 8), (4099, 32, 32), (184756, 96, 32), (184756, 64, 32),
+                                   (30001, 192, 64), (777, 64, 16), (129, 17, 5), (1, 3, 1)])
+@pytest.mark.parametrize("engine", [1, 2])
+def test_update_engines_match_fp64(mbl, n, p, q, engine):
+    """D = beta C + alpha A M (the block update of the LOBPCG step) in FP32 on the CUDA cores
+    and on the tensor cores (tcgen05, TF32 split) against numpy FP64: inputs rounded to FP32,
+    FP32 arithmetic, so |D - D64| <= c * 2^-21 * (|alpha| |A| |M| + |beta C|) elementwise."""
+    rng = np.random.default_rng(7 * n + p + q)
+    A = rng.standard_normal((n, p))
+    M = rng.standard_normal((p, q)) * np.linspace(0.5, 3.0, q)
+    C = rng.standard_normal((n, q))
+    alpha, beta = -0.75, 1.25
+    ref = beta * C + alpha * (A @ M)
+    scale = abs(alpha) * (np.abs(A) @ np.abs(M))
+    D = mbl.binding.update(_gpu(A), _gpu(M), _gpu(C), alpha, beta, "f32", engine).cpu().numpy()
+    err = np.abs(D - ref)
+    bound = scale + np.abs(beta * C)
+    assert np.all(err <= 8 * 2.0 ** -21 * bound), (err / bound).max()
+    if engine == 2:
+        # the split recovers FP32 accuracy: single-pass TF32 would leave errors near 2^-11
+        assert (err / bound).max() < 2.0 ** -18
+    # beta = 0 without C
+    D0 = mbl.binding.update(_gpu(A), _gpu(M), None, alpha, 0.0, "f32", engine).cpu().numpy()
+    assert np.all(np.abs(D0 - alpha * (A @ M)) <= 8 * 2.0 ** -21 * scale)
+    D64 = mbl.binding.update(_gpu(A), _gpu(M), _gpu(C), alpha, beta, "f64", 1).cpu().numpy()
+    assert np.abs(D64 - ref).max() <= 1e-12 * (scale.max() + np.abs(beta * C).max())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("alpha,beta", [(-1.0, 1.0), (1.0, 0.0), (1.0, 1.0), (-1.0, 0.0), (2.5, 1.0), (1.0, -0.5)])
+def test_update_scalars_and_special_values(mbl, alpha, beta):
+    """The update for the solver's scalar pairs (alpha = +-1, beta in {0, 1}) and general
+    ones, with A holding zeros, FP32-subnormal, FP64-subnormal and near-FP32-overflow
+    magnitudes next to ordinary values: every element within the FP32 bound of the FP64
+    result, on both engines."""
+    rng = np.random.default_rng(int(100 * alpha + 10 * beta) % 1000)
+    n, p, q = 128 * 40 + 3, 64, 32
+    A = rng.standard_normal((n, p))
+    A[::7, 3] = 0.0
+    A[5::11, 9] = -0.0
+    A[2::13, 17] = 1e-39 * rng.standard_normal(A[2::13, 17].shape)
+    A[3::17, 21] = 1e-310
+    A[1::19, 30] = 1e37
+    M = rng.standard_normal((p, q))
+    C = rng.standard_normal((n, q))
+    ref = beta * C + alpha * (A @ M)
+    scale = abs(alpha) * (np.abs(A) @ np.abs(M))
+    for engine in (1, 2):
+        D = mbl.binding.update(_gpu(A), _gpu(M), _gpu(C), alpha, beta, "f32", engine).cpu().numpy()
+        err = np.abs(D - ref)
+        bound = scale + np.abs(beta * C)
+        assert np.all(np.isfinite(D))
+        assert np.all(err <= 8 * 2.0 ** -21 * bound + 1e-300), (engine, (err / bound).max())
+
+
+@pytest.mark.gpu
+def test_update_engines_agree_on_padded_tiles(mbl):
+    """Ragged tails: n not a multiple of the 128-row tile, p not a multiple of the 32-wide K
+    chunk or of the 16-column box, q not a multiple of 16 -- the tensor-core result equals
+    the CUDA-core one to FP32 accuracy in every row, including the last partial tile (no
+    stale rows or columns).  Even p and q keep the rows 16-byte aligned, the condition for
+    the TMA-fed kernel; odd ones take the CUDA cores under every engine."""
+    rng = np.random.default_rng(11)
+    for n, p, q in [(128 * 152 + 1, 34, 18), (128 * 304 - 5, 190, 62), (127, 2, 2), (128 * 5, 16, 64),
+                    (128 * 152 * 3 + 77, 96, 32), (128 * 152 + 1, 33, 17), (127, 1, 1)]:
+        A = rng.standard_normal((n, p))
+        M = rng.standard_normal((p, q))
+        d1 = mbl.binding.update(_gpu(A), _gpu(M), None, 1.0, 0.0, "f32", 1).cpu().numpy()
+        d2 = mbl.binding.update(_gpu(A), _gpu(M), None, 1.0, 0.0, "f32", 2).cpu().numpy()
+        scale = np.abs(A) @ np.abs(M)
+        assert np.all(np.isfinite(d2))
+        assert np.all(np.abs(d1 - d2) <= 2.0 ** -18 * scale), (n, p, q)

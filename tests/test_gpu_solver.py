@@ -217,8 +217,9 @@ def test_bulk_copy_schedules_solve_matches_dense(mbl, mode, schedule):
 
 @pytest.mark.parametrize("L,k,nev", [(14, 32, 16), (16, 64, 24)])
 def test_tensor_core_grams_solve_matches_dense(mbl, L, k, nev):
-    """Mixed mode with its FP32 Grams on the tensor cores (tcgen05 kind::tf32, two-term
-    TF32 split): the eigenvalues nearest sigma still match dense LAPACK."""
+    """Mixed mode with its FP32 Grams and block updates on the tensor cores (tcgen05
+    kind::tf32, two-term TF32 split): the eigenvalues nearest sigma still match dense
+    LAPACK."""
     h = wl.fields(L, 8.0, 2)
     ev = np.linalg.eigvalsh(ham.dense_sector(ham.Chain(L, h, periodic=True)))
     sigma = 0.5 * (ev[0] + ev[-1])
