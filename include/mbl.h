@@ -175,7 +175,8 @@ int mbl_autotune_product(const mbl_chain *chain, int dtype, const void *X_dev, v
 /* Tuning: engine of the FP32 Gram matrices of mixed mode (S^T S, S^T A S, X^T A X; the
  * tall-skinny contraction of the Rayleigh-Ritz step, Sec. 3.2) and of its FP32 block
  * updates (the projections of W and P against X and the new direction P): 0 = default
- * (tensor cores for Grams whose sides are both >= 96, CUDA cores otherwise), 1 = CUDA cores
+ * (tensor cores for Grams whose sides are both >= 64 and for updates of at least 16,384
+ * rows, CUDA cores otherwise), 1 = CUDA cores
  * (FP32 FMA), 2 = tensor cores whenever the shape fits (tcgen05.mma kind::tf32 with FP32
  * accumulators in tensor memory; each FP32 operand split into two TF32 parts, three
  * products, error of the order of FP32 rounding; Grams up to 256 x 256, updates with
@@ -188,8 +189,11 @@ int mbl_set_gram_engine(int engine);
  * <= 256, into C (p x q, row-major, ldc >= q, FP64 device memory).  precision MBL_F64:
  * FP64 arithmetic (CUDA cores); MBL_F32: inputs rounded to FP32, products accumulated in
  * FP32 per slab of rows, slabs summed in FP64 in a fixed order, on the engine given
- * (0: the process-wide choice of mbl_set_gram_engine, 1: CUDA cores, 2: tensor cores;
- * 2 with MBL_F64 is MBL_ERR_ARG).  Workspace: mbl_gram_workspace_size bytes of device memory.
+ * (0: the process-wide choice of mbl_set_gram_engine, 1: CUDA cores, 2: tensor cores --
+ * A and B read by TMA, tcgen05.mma kind::tf32 with each operand split into two TF32 parts,
+ * the accumulators drained every 256 rows into float-float slab sums; it needs A and B
+ * 16-byte aligned with even leading dimensions and otherwise runs on the CUDA cores; 2 with
+ * MBL_F64 is MBL_ERR_ARG).  Workspace: mbl_gram_workspace_size bytes of device memory.
  * Deterministic for a given engine. */
 int mbl_gram_workspace_size(int64_t n, int p, int q, size_t *bytes);
 int mbl_gram(const double *A_dev, int64_t lda, int p, const double *B_dev, int64_t ldb, int q, int64_t n,

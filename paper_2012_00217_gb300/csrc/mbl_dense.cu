@@ -79,23 +79,24 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double *__restrict__
         }
 }
 
-// C[i][j] (ldc) = sum over slabs of part[slab][i][j]; optionally the symmetric part
-// (C + C^T)/2 when p == q and sym != 0.  A block takes 32 consecutive outputs; its 8
-// warps split the slabs (warp g sums slabs g, g + 8, ...), and one thread per output
-// adds the 8 group sums in group order, so the result is the same on every run.
+// C[i][j] (ldc) = sum over slabs of part[slab][i][j] (part[slab][j][i] when colmajor, the
+// tensor-core Gram's layout); optionally the symmetric part (C + C^T)/2 when p == q and
+// sym != 0.  A block takes 32 outputs consecutive in the partials' order; its 8 warps split
+// the slabs (warp g sums slabs g, g + 8, ...), and one thread per output adds the 8 group
+// sums in group order, so the result is the same on every run.
 constexpr int kRedGroups = 8;
 
 __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ part, int nslab, int p, int q,
-                                                     double *__restrict__ C, int64_t ldc, int sym)
+                                                     double *__restrict__ C, int64_t ldc, int sym, int colmajor)
 {
     __shared__ double s_sum[kRedGroups][32], s_tr[kRedGroups][32];
     const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + o;
     const int pq = p * q;
+    const int i = colmajor ? e % p : e / q, j = colmajor ? e / p : e % q;
     double s = 0.0, t = 0.0;
     if (e < pq) {
-        const int i = e / q, j = e % q;
-        const int64_t et = (int64_t)j * q + i;
+        const int64_t et = colmajor ? (int64_t)i * p + j : (int64_t)j * q + i;
         for (int b = g; b < nslab; b += kRedGroups) {
             s += part[(int64_t)b * pq + e];
             if (sym) t += part[(int64_t)b * pq + et];
@@ -110,7 +111,6 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ 
             a += s_sum[h][o];
             c += s_tr[h][o];
         }
-        const int i = e / q, j = e % q;
         C[(int64_t)i * ldc + j] = sym ? 0.5 * (a + c) : a;
     }
 }
@@ -146,15 +146,14 @@ void set_gram_engine(int engine) { g_gram_engine = engine; }
 void set_gram_engine_local(int engine) { t_gram_engine = engine; }
 
 // FP32 Grams go to the tensor cores when selected and the shape fits (p, q <= 256).  By
-// default only when both sides are >= 96: the 128-row accumulator tile is then mostly
-// used (measured at n = 184,756: 96 x 96 in 255 us against 609 us on the CUDA cores,
-// 192 x 192 at n = 10.4 M in 35 ms against 70 ms; 64 x 64 and smaller are faster on the
-// CUDA cores).
+// default when both sides are >= 64 (measured with the TMA-fed kernel at n = 184,756:
+// S^T S 96 x 96 in 96 us against 576 us on the CUDA cores, 64 x 64 in 89 us against 147 us;
+// at n = 705,432, 192 x 192 in 1.0 ms against 4.1 ms; 32 x 32 is a tie).
 static bool use_tensor_cores(int p, int q)
 {
     const int e = t_gram_engine ? t_gram_engine : g_gram_engine;
     if (e == 1 || !gram_tc_supported(p, q)) return false;
-    return e == 2 || (p >= 96 && q >= 96);
+    return e == 2 || (p >= 64 && q >= 64);
 }
 
 // FP32 block updates on the tensor cores: when asked for (engine 2) or by default from
@@ -183,12 +182,12 @@ static void launch_gram(const double *A, int64_t lda, int p, const double *B, in
 int gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n, double *C,
          int64_t ldc, int sym, int compute_f32, double *part, cudaStream_t st)
 {
-    if (compute_f32 && use_tensor_cores(p, q)) {
+    if (compute_f32 && use_tensor_cores(p, q) && gram_tc_eligible(A, lda, p, B, ldb, q)) {
         const int nslab = gram_tc_slabs(n, p);
         const int rc = gram_tc_partial(A, lda, p, B, ldb, q, n, nslab, part, st);
         if (rc != MBL_OK) return rc;
         note_launch();
-        k_gram_reduce<<<(p * q + 31) / 32, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym);
+        k_gram_reduce<<<(p * q + 31) / 32, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym, 1);
         return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
     }
     const int nslab = gram_slabs(n, p, q);
@@ -204,7 +203,7 @@ int gram(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int 
         else launch_gram<double, 16>(A, lda, p, B, ldb, q, n, rps, nslab, part, st);
     }
     note_launch();
-    k_gram_reduce<<<(p * q + 31) / 32, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym);
+    k_gram_reduce<<<(p * q + 31) / 32, 256, 0, st>>>(part, nslab, p, q, C, ldc, sym, 0);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
 

@@ -18,8 +18,10 @@ size_t gram_partial_doubles(int64_t n, int p, int q);
 // cores (tcgen05).
 void set_gram_engine(int engine);
 void set_gram_engine_local(int engine);  // this thread's next Grams (0: use the switch)
-// Tensor-core slab partials (mbl_gram_tc.cu): part[slab][i][j] for nslab slabs.
+// Tensor-core slab partials (mbl_gram_tc.cu): part[slab][i][j] for nslab slabs; the blocks
+// are read by TMA, so they must be 16-byte aligned with even leading dimensions.
 bool gram_tc_supported(int p, int q);
+bool gram_tc_eligible(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q);
 int gram_tc_slabs(int64_t n, int p);
 int gram_tc_partial(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n, int nslab,
                     double *part, cudaStream_t st);

@@ -1,20 +1,17 @@
-// mbl_gram_tc.cu -- the tall-skinny Gram C = A^T B of the LOBPCG Rayleigh-Ritz step
-// (Sec. 3.2: the block method's dense contraction) on the 5th-generation tensor cores of
-// sm_103a: tcgen05.mma kind::tf32 with the accumulator in tensor memory (TMEM).
+// mbl_gram_tc.cu -- the dense contractions of the LOBPCG step (Sec. 3.2: the block method's
+// Grams and block updates) on the 5th-generation tensor cores of sm_103a: tcgen05.mma
+// kind::tf32 with the accumulators in tensor memory (TMEM), operands moved by TMA.
 //
-// FP32 accuracy from TF32 operands: every FP64 input x is rounded once to FP32, then
-// split x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (x - hi is exact in FP32), and
-// D += Ahi Bhi + Ahi Blo + Alo Bhi; the dropped Alo Blo and the rounding of lo are below
-// 2^-21 relative, the order of FP32's own rounding.
+// FP32 accuracy from TF32 operands: every FP64 input x is cut to FP32 and split into
+// x = hi + lo, hi and lo TF32 (by bit operations: conversions and arithmetic on GB300's FP64
+// pipe would bind these HBM-bound kernels), and D += Ahi Bhi + Ahi Blo + Alo Bhi; the dropped
+// Alo Blo and the rounding of lo are below 2^-21 relative, the order of FP32's own rounding.
 //
-// Work split: block (m_tile, slab) owns the 128 x Np accumulator of columns
-// [128 m_tile, +128) of A against all Np (>= q, multiple of 16) columns of B over a slab
-// of rows, and writes it as one slab partial (FP64) for the fixed-order slab reduction
-// of mbl_dense.cu.  Rows are staged 32 at a time (four MMA k-steps of 8), converted and
-// split by all 256 threads into two shared-memory buffers (K-major, no swizzle: 8-row x
-// 16-byte core matrices, 128 B apart along K, 1024 B apart along M/N); one thread issues
-// the MMAs of a chunk and commits them to the buffer's mbarrier, which the next use of
-// that buffer waits on, so staging of chunk i+1 overlaps the MMAs of chunk i.
+// Both kernels are persistent (one CTA per SM) with warp roles joined by mbarriers: a TMA
+// producer fills a ring of 128-byte-swizzled FP64 boxes, converter warps write the TF32
+// operand tiles (no-swizzle K-major core matrices: 8 rows x 16 bytes, 128 B apart along K),
+// one thread issues the MMAs, and epilogue warps read the accumulators with tcgen05.ld.
+// Every ring and mbarrier has one waiting role that waits on each of its phases in turn.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -28,13 +25,12 @@ namespace mbl {
 namespace {
 
 constexpr int kTcM = 128;        // accumulator rows (M of the MMA)
-constexpr int kTcKC = 32;        // rows of A and B staged per chunk
-constexpr int kTcThreads = 256;  // 8 warps
+constexpr int kTcKC = 32;        // K per staged chunk of the update's M operand
 constexpr long long kTcWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
-// Operand tile of R rows (R a multiple of 8) and kTcKC K-elements: byte offset of the
-// 4-element K quad kq of row r.  Core matrices (8 rows x 16 B) are 128 B apart along K
-// and 1024 B apart along the rows.
+// Operand tile of R rows (R a multiple of 8) and kTcKC K-elements (the update's staged M):
+// byte offset of the 4-element K quad kq of row r.  Core matrices (8 rows x 16 B) are 128 B
+// apart along K and 1024 B apart along the rows.
 __device__ __forceinline__ uint32_t tile_offset(int r, int kq) { return (uint32_t)((r >> 3) * 1024 + kq * 128 + (r & 7) * 16); }
 
 __host__ __device__ constexpr uint32_t tile_bytes(int rows) { return (uint32_t)rows * kTcKC * 4u; }
@@ -46,19 +42,6 @@ __device__ __forceinline__ float to_tf32(float x)
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading byte offset (between
-// core matrices along K), stride byte offset (between 8-row groups), descriptor version
-// 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
 }
 
 // Instruction descriptor, kind::tf32: D in FP32, A and B in TF32, both K-major,
@@ -104,127 +87,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *m)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(m))
                  : "memory");
-}
-
-// Stage rows [r0, r0 + kTcKC) of columns [c0, c0 + cols) of X (row-major, ld) as the hi
-// and lo TF32 parts of an R-row operand tile; rows past n and columns past cols are 0.
-__device__ __forceinline__ void stage(const double *__restrict__ X, int64_t ld, int64_t n, int64_t r0, int c0,
-                                      int cols, int R, float *hi, float *lo)
-{
-    for (int task = threadIdx.x; task < R * (kTcKC / 4); task += kTcThreads) {
-        const int r = task % R, kq = task / R;
-        float h[4], l[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int64_t row = r0 + 4 * kq + i;
-            const float x = (row < n && r < cols) ? (float)__ldg(X + row * ld + c0 + r) : 0.0f;
-            h[i] = to_tf32(x);
-            l[i] = to_tf32(x - h[i]);
-        }
-        const uint32_t off = tile_offset(r, kq) / 4;
-        *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-    }
-}
-
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_gram_tc(const double *__restrict__ A, int64_t lda, int p, const double *__restrict__ B, int64_t ldb, int q,
-              int np, int64_t n, int64_t rows_per_slab, double *__restrict__ part, uint32_t tmem_cols)
-{
-    extern __shared__ __align__(1024) unsigned char tc_raw[];
-    __shared__ __align__(8) uint64_t s_mbar[2];
-    __shared__ uint32_t s_tmem;
-    const int m_tile = blockIdx.x, slab = blockIdx.y;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t a_bytes = tile_bytes(kTcM), b_bytes = tile_bytes(np);
-    const uint32_t buf_bytes = 2 * a_bytes + 2 * b_bytes;  // A hi, A lo, B hi, B lo
-    if (threadIdx.x == 0) {
-        mbar_init(&s_mbar[0], 1);
-        mbar_init(&s_mbar[1], 1);
-    }
-    __syncwarp();
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
-                     "r"(tmem_cols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = s_tmem;
-    const uint32_t idesc = instr_desc_tf32(np);
-    const int c0 = m_tile * kTcM, acols = min(kTcM, p - c0);
-    const int64_t r_begin = (int64_t)slab * rows_per_slab;
-    const int64_t r_end = min(n, r_begin + rows_per_slab);
-    const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + kTcKC - 1) / kTcKC) : 0;
-    bool ok = true;
-    for (int i = 0; i < nchunks; ++i) {
-        const int b = i & 1;
-        if (i >= 2) ok = ok && mbar_wait(&s_mbar[b], (unsigned)(((i - 2) >> 1) & 1));
-        __syncwarp();
-        if (!__syncthreads_and(ok)) break;
-        unsigned char *base = tc_raw + b * buf_bytes;
-        float *ahi = reinterpret_cast<float *>(base), *alo = reinterpret_cast<float *>(base + a_bytes);
-        float *bhi = reinterpret_cast<float *>(base + 2 * a_bytes);
-        float *blo = reinterpret_cast<float *>(base + 2 * a_bytes + b_bytes);
-        const int64_t r0 = r_begin + (int64_t)i * kTcKC;
-        stage(A, lda, r_end, r0, c0, acols, kTcM, ahi, alo);
-        stage(B, ldb, r_end, r0, 0, q, np, bhi, blo);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = saddr(ahi), a1 = saddr(alo), b0 = saddr(bhi), b1 = saddr(blo);
-#pragma unroll
-            for (int s = 0; s < kTcKC / 8; ++s) {
-                const uint32_t ks = (uint32_t)s * 256u;  // two core matrices along K per step
-                mma_tf32(tmem, smem_desc(a0 + ks), smem_desc(b0 + ks), idesc, (i > 0 || s > 0) ? 1 : 0);
-                mma_tf32(tmem, smem_desc(a0 + ks), smem_desc(b1 + ks), idesc, 1);
-                mma_tf32(tmem, smem_desc(a1 + ks), smem_desc(b0 + ks), idesc, 1);
-            }
-            mma_commit(&s_mbar[b]);
-        }
-        __syncwarp();
-    }
-    // the last commit covers every MMA of the block
-    if (nchunks > 0) {
-        const int last = nchunks - 1;
-        const bool done = mbar_wait(&s_mbar[last & 1], (unsigned)((last >> 1) & 1));
-        ok = ok && done;
-        if (!done && nchunks > 1) mbar_wait(&s_mbar[(last - 1) & 1], (unsigned)(((last - 1) >> 1) & 1));
-    }
-    __syncwarp();
-    ok = __syncthreads_and(ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // accumulator -> slab partial: warp w reads TMEM lanes 32 (w % 4) .. +31 and every
-    // other 8-column group (w / 4 picks which)
-    double *out = part + (int64_t)slab * p * q;
-    const int quad = warp & 3, half = warp >> 2;
-    const int row = c0 + quad * 32 + lane;
-    for (int cg = half; cg * 8 < np; cg += 2) {
-        uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (nchunks > 0) {
-            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cg * 8);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        }
-        if (row < p) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int col = cg * 8 + j;
-                if (col < q) out[(int64_t)row * q + col] = ok ? (double)__uint_as_float(v[j]) : (double)NAN;
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
 // ---------------------------------------------------------------------------------
@@ -402,6 +264,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
                  : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
                    "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
                    "+r"(v[15])
+                 :
+                 : "memory");
+}
+
+// 8 accumulator columns, as tmem_ld16
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
                  :
                  : "memory");
 }
@@ -683,6 +557,284 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
 }
 
 // ---------------------------------------------------------------------------------
+// Gram C = A^T B (A: n x p, B: n x q, FP64 in memory; p, q <= 256) with FP32 accuracy on the
+// tensor cores, fed by TMA: the same ring protocol, bit-level TF32 split and warp roles as
+// the block update above, with the contraction now over the rows.  One persistent CTA per
+// SM owns a slab of rows (a multiple of 16) and accumulates the p x q Gram of its slab in
+// tensor memory (M = 128 columns of A per accumulator tile, N = q padded to 16); the slab
+// partials are summed in a fixed order by the reduction kernel of mbl_dense.cu.  The tensor
+// core rounds its FP32 accumulator once per MMA (toward zero, as measured: a 1,216-row slab of
+// same-sign terms, the diagonal of S^T S, drifted by 2.5e-5), so
+//   - the small products Ahi Blo + Alo Bhi go to an accumulator of their own, leaving one
+//     rounding of the full-size accumulator per k-step,
+//   - the accumulators are drained every 16 chunks (256 rows; 8 when the correction
+//     accumulators do not fit in tensor memory) into the slab partial, kept as a float-float
+//     pair (TwoSum, no FP64 pipe) and widened to FP64 at the end,
+//   - two accumulator sets, where they fit, let the MMAs run on while one is drained.
+//   warp 24      producer: per 16-row chunk, the 16-column boxes of A (and of B when B is
+//                not A) into one ring slot,
+//   warps 8-23   converters: each chunk transposed into K-major TF32 hi/lo operand tiles (the
+//                K index is the row of A): lanes read 16 consecutive columns of one row of a
+//                swizzled box, write 8 consecutive 16-byte core-matrix rows,
+//   warp 25      MMA issuer: per chunk and accumulator tile, two k-steps of three MMAs,
+//   warps 0-7    epilogue: per drain, tcgen05.ld of the accumulators (warp w: lanes
+//                32 (w % 4) .. +31, alternate 16-column groups by w / 4) into the partial.
+// When B is A (S^T S) the B operand is the A tile itself.
+constexpr int kGrKC = 16;                          // rows (K) per chunk
+constexpr int kGrBoxBytes = kGrKC * 16 * 8;        // 16 rows x 16 FP64 columns
+constexpr int kGrThreads = 832;                    // 26 warps
+constexpr int kGrConvThreads = 512;                // warps 8-23
+constexpr int kGrEpiThreads = 256;                 // warps 0-7
+constexpr int kGrMaxStages = 8;
+
+struct GrBars {
+    uint64_t full[kGrMaxStages], empty[kGrMaxStages], afull[2], aempty[2], accfull[2], accempty[2], done;
+};
+
+// (hi, lo) += v exactly up to the rounding of lo (Knuth's TwoSum on hi)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v)
+{
+    const float s = hi + v, bb = s - hi;
+    const float e = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += e;
+}
+
+__global__ void __launch_bounds__(kGrThreads, 1)
+    k_gram_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int p, int q,
+               int same, int ma, int np, int64_t n, int64_t rows_per_slab, double *__restrict__ part, int nstages,
+               int nacc, int split, int drain, uint32_t tmem_cols)
+{
+    extern __shared__ unsigned char gr_raw[];
+    __shared__ __align__(8) GrBars bars;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_err;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nba = (p + 15) / 16, nbb = same ? 0 : (q + 15) / 16;  // boxes per chunk
+    const int nrows_b = same ? 0 : np;                             // rows of a separate B tile
+    const uint32_t slot_bytes = (uint32_t)(nba + nbb) * kGrBoxBytes;
+    const uint32_t buf_bytes = (uint32_t)(ma + nrows_b) * kGrKC * 4u * 2u;  // [A hi, A lo, B hi, B lo]
+    const uint32_t raw0 = saddr(gr_raw);
+    const uint32_t pad = ((raw0 + 1023u) & ~1023u) - raw0;
+    unsigned char *ring = gr_raw + pad;
+    unsigned char *obuf = ring + (size_t)nstages * slot_bytes;
+    const int mtiles = ma / kTcM;
+    const int64_t r_begin = (int64_t)blockIdx.x * rows_per_slab;
+    const int64_t r_end = min(n, r_begin + rows_per_slab);
+    const int total = r_end > r_begin ? (int)((r_end - r_begin + kGrKC - 1) / kGrKC) : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nstages; ++s) {
+            mbar_init(&bars.full[s], 1);
+            mbar_init(&bars.empty[s], kGrConvThreads);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars.afull[b], kGrConvThreads);
+            mbar_init(&bars.aempty[b], 1);
+            mbar_init(&bars.accfull[b], 1);
+            mbar_init(&bars.accempty[b], kGrEpiThreads);
+        }
+        mbar_init(&bars.done, 1);
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const int nper = (total + drain - 1) / drain;  // accumulator periods
+    const int nsub = split ? 2 : 1;                 // accumulators per tile: full-size [, correction]
+    if (warp == 25) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 24) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (; issued < total && !s_err; ++issued) {
+                const int s = issued % nstages, u = issued / nstages;
+                if (u >= 1 && !mbar_wait(&bars.empty[s], (unsigned)((u - 1) & 1))) {
+                    s_err = 1;
+                    break;
+                }
+                const int y = (int)(r_begin + (int64_t)issued * kGrKC);
+                const uint32_t dst = saddr(ring + (size_t)s * slot_bytes);
+                mbar_expect(&bars.full[s], slot_bytes);
+                for (int b = 0; b < nba; ++b) tma_load_box(dst + b * kGrBoxBytes, &tmA, 16 * b, y, &bars.full[s]);
+                for (int b = 0; b < nbb; ++b)
+                    tma_load_box(dst + (nba + b) * kGrBoxBytes, &tmB, 16 * b, y, &bars.full[s]);
+            }
+            for (int pos = issued > nstages ? issued - nstages : 0; pos < issued; ++pos)
+                if (!mbar_wait(&bars.full[pos % nstages], (unsigned)((pos / nstages) & 1))) s_err = 1;
+        }
+        __syncwarp();
+    } else if (warp == 25) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc_tf32(np);
+            for (int g = 0; g < total && !s_err; ++g) {
+                const int b = g & 1, ub = g >> 1;
+                const int per = g / drain, a = per % nacc, ua = per / nacc;
+                const bool first = g % drain == 0;
+                if (first && ua >= 1 && !mbar_wait(&bars.accempty[a], (unsigned)((ua - 1) & 1))) {
+                    s_err = 1;
+                    break;
+                }
+                if (!mbar_wait(&bars.afull[b], (unsigned)(ub & 1))) {
+                    s_err = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = saddr(obuf + (size_t)b * buf_bytes);
+                const uint32_t a_hi = base, a_lo = base + (uint32_t)ma * kGrKC * 4u;
+                const uint32_t b_hi = same ? a_hi : base + (uint32_t)ma * kGrKC * 8u;
+                const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)nrows_b * kGrKC * 4u;
+                for (int m = 0; m < mtiles; ++m) {
+                    const uint32_t d_tmem = tmem + (uint32_t)(((a * mtiles + m) * nsub) * np);
+                    const uint32_t c_tmem = d_tmem + (uint32_t)((nsub - 1) * np);  // = d_tmem without split
+                    const uint32_t mo = (uint32_t)m * (kTcM / 8) * 512u;  // 128 rows of the A tile
+#pragma unroll
+                    for (int s2 = 0; s2 < kGrKC / 8; ++s2) {
+                        const uint32_t ks = (uint32_t)s2 * 256u;
+                        const uint64_t dA0 = smem_desc_sbo(a_hi + mo + ks, 512u), dA1 = smem_desc_sbo(a_lo + mo + ks, 512u);
+                        const uint64_t dB0 = smem_desc_sbo(b_hi + ks, 512u), dB1 = smem_desc_sbo(b_lo + ks, 512u);
+                        mma_tf32(d_tmem, dA0, dB0, idesc, (!first || s2 > 0) ? 1 : 0);
+                        mma_tf32(c_tmem, dA0, dB1, idesc, (!first || s2 > 0 || !split) ? 1 : 0);
+                        mma_tf32(c_tmem, dA1, dB0, idesc, 1);
+                    }
+                }
+                mma_commit(&bars.aempty[b]);
+                if (g % drain == drain - 1 || g == total - 1) mma_commit(&bars.accfull[a]);
+            }
+            mma_commit(&bars.done);
+            if (!mbar_wait(&bars.done, 0u)) s_err = 1;
+        }
+        __syncwarp();
+    } else if (warp >= 8) {
+        // ---------------- converters: chunk -> K-major TF32 tiles (K = row of A / B) ----------------
+        const int cw = warp - 8;
+        const int wa = (ma / 16) * 2, wb = (nrows_b / 16) * 2;  // warp items: 16 columns x 2 K-quads
+        const int col16 = lane & 15, kqo = lane >> 4;
+        for (int g = 0; g < total && !s_err; ++g) {
+            const int s = g % nstages, u = g / nstages, b = g & 1, ub = g >> 1;
+            if (!mbar_wait(&bars.full[s], (unsigned)(u & 1)) ||
+                (ub >= 1 && !mbar_wait(&bars.aempty[b], (unsigned)((ub - 1) & 1)))) {
+                s_err = 1;
+                break;
+            }
+            const unsigned char *slot = ring + (size_t)s * slot_bytes;
+            unsigned char *base = obuf + (size_t)b * buf_bytes;
+            for (int wi = cw; wi < wa + wb; wi += 16) {
+                const bool is_a = wi < wa;
+                const int wl = is_a ? wi : wi - wa;
+                const int c = 16 * (wl >> 1) + col16;           // column of A (or B) = tile row
+                const int kq = 2 * (wl & 1) + kqo;              // rows 4 kq .. 4 kq + 3 of the chunk
+                const int nb = is_a ? nba : (q + 15) / 16;
+                const unsigned char *box = slot + (size_t)((is_a ? 0 : nba) + c / 16) * kGrBoxBytes;
+                double x[4] = {0.0, 0.0, 0.0, 0.0};
+                if (c < 16 * nb) {  // columns past p (q) inside the last box were zero-filled
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = 4 * kq + i;
+                        x[i] = *reinterpret_cast<const double *>(box + swz_off(r, col16 >> 1) + (col16 & 1) * 8);
+                    }
+                }
+                float h[4], l[4];
+                split_tf32x4(x, h, l);
+                const int rows = is_a ? ma : nrows_b;
+                float *hi = reinterpret_cast<float *>(base + (is_a ? 0 : (size_t)ma * kGrKC * 8));
+                float *lo = hi + rows * kGrKC;
+                const uint32_t off = tile16_offset(c, kq) / 4;
+                *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+            mbar_arrive1(&bars.empty[s]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive1(&bars.afull[b]);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: drain each accumulator period into the partial ----------------
+        const int quad = warp & 3, half = warp >> 2;
+        // the slab partial is column-major (element (i, j) at j p + i): a warp's 32 rows of one
+        // column are 32 consecutive elements; (hi, lo) pairs live in its own storage until the end
+        double *out = part + (int64_t)blockIdx.x * p * q;
+        float2 *acc2 = reinterpret_cast<float2 *>(out);
+        bool ok = !s_err;
+        for (int per = 0; per < nper; ++per) {
+            const int a = per % nacc, ua = per / nacc;
+            ok = ok && !s_err && mbar_wait(&bars.accfull[a], (unsigned)(ua & 1));
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int m = 0; m < mtiles; ++m) {
+                const int row = m * kTcM + 32 * quad + lane;
+                for (int g8 = half; g8 * 8 < np; g8 += 2) {
+                    const uint32_t t0 = tmem + (uint32_t)(((a * mtiles + m) * nsub) * np + 8 * g8) +
+                                        ((uint32_t)(32 * quad) << 16);
+                    // the partial's 8 (hi, lo) pairs first, so their loads fly during the TMEM reads
+                    float2 c2[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int col = 8 * g8 + e;
+                        c2[e] = make_float2(0.0f, 0.0f);
+                        if (per > 0 && row < p && col < q) c2[e] = acc2[(int64_t)col * p + row];
+                    }
+                    uint32_t v[8], w[8];
+                    __syncwarp();
+                    tmem_ld8(t0, v);
+                    if (split) {
+                        tmem_ld8(t0 + (uint32_t)np, w);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) w[e] = 0u;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int col = 8 * g8 + e;
+                        two_sum_acc(c2[e].x, c2[e].y, __uint_as_float(v[e]));
+                        two_sum_acc(c2[e].x, c2[e].y, __uint_as_float(w[e]));
+                        if (row < p && col < q) acc2[(int64_t)col * p + row] = c2[e];
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive1(&bars.accempty[a]);
+        }
+        // widen the pairs in place: each thread the elements it drained (its row, its 8-column groups)
+        for (int m = 0; m < mtiles && ok; ++m) {
+            const int row = m * kTcM + 32 * quad + lane;
+            if (row < p)
+                for (int col = 8 * half; col < q; col += (col % 8 == 7) ? 9 : 1) {
+                    const int64_t e = (int64_t)col * p + row;
+                    const float2 c2 = nper > 0 ? acc2[e] : make_float2(0.0f, 0.0f);
+                    out[e] = f32_to_f64_fast(c2.x) + f32_to_f64_fast(c2.y);
+                }
+        }
+        if (!ok) s_err = 1;
+        __syncwarp();
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_err) {  // the reduction's finiteness reports it
+        double *out = part + (int64_t)blockIdx.x * p * q;
+        for (int e = threadIdx.x; e < p * q; e += kGrThreads) out[e] = (double)NAN;
+    }
+    __syncwarp();
+    if (warp == 25)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// ---------------------------------------------------------------------------------
 // Host side of the tensor maps: the driver's encoder, looked up once through the runtime.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -703,14 +855,14 @@ EncodeTiledFn tensor_map_encoder()
 }
 
 // An FP64 row-major matrix (rows x cols, leading dimension ld) as a 2-D tensor map with
-// 16-column x 128-row boxes and 128-byte swizzle.
-bool fp64_box_map(CUtensorMap *m, const double *base, int64_t rows, int cols, int64_t ld)
+// 16-column x box_rows-row boxes and 128-byte swizzle.
+bool fp64_box_map(CUtensorMap *m, const double *base, int64_t rows, int cols, int64_t ld, int box_rows = kTcM)
 {
     const EncodeTiledFn enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(double)};
-    const cuuint32_t box[2] = {16, (cuuint32_t)kTcM};
+    const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -751,35 +903,77 @@ UpdConfig update_config(int p, int q)
 
 bool gram_tc_supported(int p, int q) { return p >= 1 && q >= 1 && p <= 256 && q <= 256; }
 
+namespace {
+
+// A ring of at least two chunks next to two operand buffers; 0 if it does not fit
+int gram_stages(int p, int q, bool same)
+{
+    const int ma = (p + kTcM - 1) / kTcM * kTcM, np = (q + 15) / 16 * 16;
+    const size_t slot = (size_t)((p + 15) / 16 + (same ? 0 : (q + 15) / 16)) * kGrBoxBytes;
+    const size_t fixed = 1024 + (size_t)2 * (ma + (same ? 0 : np)) * kGrKC * 4 * 2;
+    if (fixed >= (size_t)kUpdSmemMax) return 0;
+    const int ns = (int)(((size_t)kUpdSmemMax - fixed) / slot);
+    return ns > kGrMaxStages ? kGrMaxStages : ns;
+}
+
+bool gram_same(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q)
+{
+    return A == B && lda == ldb && p == q;
+}
+
+}  // namespace
+
+bool gram_tc_eligible(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q)
+{
+    if (!gram_tc_supported(p, q) || !tensor_map_encoder()) return false;
+    if (!tma_addressable(A, lda) || !tma_addressable(B, ldb)) return false;
+    return gram_stages(p, q, gram_same(A, lda, p, B, ldb, q)) >= 2;
+}
+
 int gram_tc_slabs(int64_t n, int p)
 {
-    const int mtiles = (p + kTcM - 1) / kTcM;
-    int want = num_sms() / mtiles;
-    const int64_t by_rows = (n + 4 * kTcKC - 1) / (4 * kTcKC);  // at least 128 rows per slab
-    if (want > by_rows) want = (int)by_rows;
-    return want < 1 ? 1 : want;
+    (void)p;
+    int64_t want = num_sms();
+    const int64_t by_rows = (n + 8 * kGrKC - 1) / (8 * kGrKC);  // at least 128 rows per slab
+    if (want > by_rows) want = by_rows;
+    return want < 1 ? 1 : (int)want;
 }
 
 int gram_tc_partial(const double *A, int64_t lda, int p, const double *B, int64_t ldb, int q, int64_t n, int nslab,
                     double *part, cudaStream_t st)
 {
-    if (!gram_tc_supported(p, q)) return MBL_ERR_ARG;
-    const int np = (q + 15) / 16 * 16;
-    const uint32_t tmem_cols = np <= 32 ? 32u : (np <= 64 ? 64u : (np <= 128 ? 128u : 256u));
-    const size_t smem = 2 * (size_t)(2 * tile_bytes(kTcM) + 2 * tile_bytes(np));
+    if (!gram_tc_eligible(A, lda, p, B, ldb, q) || n > ((int64_t)1 << 31) || nslab < 1) return MBL_ERR_ARG;
+    const bool same = gram_same(A, lda, p, B, ldb, q);
+    CUtensorMap ta, tb;
+    if (!fp64_box_map(&ta, A, n > 0 ? n : 1, p, lda, kGrKC) || !fp64_box_map(&tb, B, n > 0 ? n : 1, q, ldb, kGrKC))
+        return MBL_ERR_ARG;
+    const int ma = (p + kTcM - 1) / kTcM * kTcM, np = (q + 15) / 16 * 16;
+    // accumulator layout: with a correction accumulator per tile when it fits, two sets when
+    // those fit too
+    const int tile_cols = (ma / kTcM) * np;
+    int split = 1, nacc = 2, drain = 16;
+    if (4 * tile_cols > 512) nacc = 1;
+    if (2 * tile_cols > 512) {
+        split = 0;
+        nacc = 2 * tile_cols <= 512 ? 2 : 1;
+        drain = 8;
+    }
+    const int cols = nacc * (split ? 2 : 1) * tile_cols;
+    const uint32_t tmem_cols = cols <= 32 ? 32u : (cols <= 64 ? 64u : (cols <= 128 ? 128u : (cols <= 256 ? 256u : 512u)));
+    const int ns = gram_stages(p, q, same);
+    const size_t slot = (size_t)((p + 15) / 16 + (same ? 0 : (q + 15) / 16)) * kGrBoxBytes;
+    const size_t smem = 1024 + (size_t)2 * (ma + (same ? 0 : np)) * kGrKC * 4 * 2 + (size_t)ns * slot;
     static const bool attr = []() {
-        cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * (2 * tile_bytes(kTcM) + 2 * tile_bytes(256))));
+        cudaFuncSetAttribute(k_gram_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpdSmemMax);
         return true;
     }();
     (void)attr;
-    const int64_t rps = ((n + nslab - 1) / nslab + kTcKC - 1) / kTcKC * kTcKC;
-    dim3 grid((p + kTcM - 1) / kTcM, nslab);
+    const int64_t rps = ((n + nslab - 1) / nslab + kGrKC - 1) / kGrKC * kGrKC;
     note_launch();
-    k_gram_tc<<<grid, kTcThreads, smem, st>>>(A, lda, p, B, ldb, q, np, n, rps, part, tmem_cols);
+    k_gram_tma<<<nslab, kGrThreads, smem, st>>>(ta, tb, p, q, same ? 1 : 0, ma, np, n, rps, part, ns, nacc, split,
+                                                 drain, tmem_cols);
     return cudaGetLastError() == cudaSuccess ? MBL_OK : MBL_ERR_CUDA;
 }
-
 
 bool update_tc_supported(const double *A, int64_t lda, int p, int q, const double *C, int64_t ldc, const double *D,
                          int64_t ldd, double beta)

@@ -406,6 +406,23 @@ def test_gram_engines_match_fp64(mbl, n, p, q, engine):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("n,p", [(1000, 8), (4099, 32), (20000, 96), (184756, 96), (30001, 192), (777, 256),
+                                 (17, 5), (33, 130)])
+def test_gram_of_a_block_with_itself(mbl, n, p):
+    """S^T S (one operand read once, the same tensor-core tile serving both sides) on both
+    engines against numpy FP64, within 8 * 2^-21 of |S|^T |S|; the result is symmetric to
+    the same accuracy."""
+    rng = np.random.default_rng(3 * n + p)
+    S = rng.standard_normal((n, p)) * np.linspace(0.25, 4.0, p)
+    ref = S.T @ S
+    scale = np.abs(S).T @ np.abs(S)
+    for engine in (1, 2):
+        G = mbl.binding.gram(_gpu(S), _gpu(S), "f32", engine).cpu().numpy()
+        assert np.all(np.abs(G - ref) <= 8 * 2.0 ** -21 * scale), (engine, (np.abs(G - ref) / scale).max())
+        assert np.all(np.abs(G - G.T) <= 16 * 2.0 ** -21 * scale)
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("n,p,q", [(1000, 8, 8), (4099, 32, 32), (184756, 96, 32), (184756, 64, 32),
                                    (30001, 192, 64), (777, 64, 16), (129, 17, 5), (1, 3, 1)])
 @pytest.mark.parametrize("engine", [1, 2])
