@@ -661,9 +661,18 @@ def run_profile(args):
             del A
     elif args.profile == "step":
         # one bench step exactly as timed (products autotuned first, one warm-up step), the
-        # timed step inside the NVTX range "step" for a launch list restricted to it
+        # timed step inside the NVTX range "step" for a launch list restricted to it.  Under
+        # a profiler the autotuner's timings are distorted, so --pin sets the product choices
+        # a plain bench run reported instead (schedule,lane_bytes,tile_bits for FP32 then FP64)
         s = _setup(torch, mbl, dev)
-        autotune_step(torch, mbl, dev, s)
+        if args.pin:
+            vals = [int(v) for v in args.pin.split(",")]
+            for off, tdt in ((0, torch.float32), (3, torch.float64)):
+                mbl.binding.set_product_schedule(s["k"], tdt, vals[off])
+                mbl.binding.set_product_lane_bytes(s["k"], tdt, vals[off + 1])
+                mbl.binding.set_product_tile_bits(s["k"], tdt, vals[off + 2])
+        else:
+            autotune_step(torch, mbl, dev, s)
         step = Step(torch, mbl, dev, s, mbl.MODE_MIXED)
         step.run()
         torch.cuda.synchronize()
@@ -716,6 +725,8 @@ def main():
                     help="time the CPU oracle only (product sweep and small whole solves) on this host")
     ap.add_argument("--cpu-sweep-L", default="22,24,26", help="chain lengths of the oracle product sweep")
     ap.add_argument("--cpu-sweep-no-solves", action="store_true", help="product sweep only")
+    ap.add_argument("--pin", default="", help="with --profile step: the product choices to use instead of "
+                    "autotuning, 'schedule,lane_bytes,tile_bits' for FP32 then FP64 (e.g. 3,32,10,2,64,13)")
     ap.add_argument("--profile", choices=["product", "pcg", "bounds", "gram", "batch", "step"], default=None,
                     help="profiling driver: only run the block products (L=20 k=32 FP32 and L=26 k=64 "
                          "FP32), a short solve (2 iterations x 30 PCG steps), the spectrum bounds or the "
