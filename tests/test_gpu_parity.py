@@ -479,6 +479,41 @@ def test_update_scalars_and_special_values(mbl, alpha, beta):
 
 
 @pytest.mark.gpu
+def test_tensor_core_dispatch_and_fallback(mbl):
+    """Engine 2 takes the TMA-fed tensor-core kernels for aligned blocks with even leading
+    dimensions (their TF32-split result differs from the CUDA cores' FP32 FMA in the low
+    bits) and falls back to the CUDA cores, with the same accuracy, for a block that starts
+    8 bytes past a 16-byte boundary or has an odd leading dimension."""
+    rng = np.random.default_rng(21)
+    n, p, q = 128 * 40 + 5, 64, 32
+    A = rng.standard_normal((n, p))
+    M = rng.standard_normal((p, q))
+    ref_u = A @ M
+    ref_g = A.T @ A
+    su = np.abs(A) @ np.abs(M)
+    sg = np.abs(A).T @ np.abs(A)
+    d1 = mbl.binding.update(_gpu(A), _gpu(M), None, 1.0, 0.0, "f32", 1).cpu().numpy()
+    d2 = mbl.binding.update(_gpu(A), _gpu(M), None, 1.0, 0.0, "f32", 2).cpu().numpy()
+    g1 = mbl.binding.gram(_gpu(A), _gpu(A), "f32", 1).cpu().numpy()
+    g2 = mbl.binding.gram(_gpu(A), _gpu(A), "f32", 2).cpu().numpy()
+    assert not np.array_equal(d1, d2) and not np.array_equal(g1, g2)
+    # an n x p view one double past the start of a padded buffer: 8-byte aligned only
+    big = _gpu(np.concatenate([np.zeros(1), A.ravel()]))
+    Av = big[1:].view(n, p)
+    assert Av.data_ptr() % 16 == 8
+    du = mbl.binding.update(Av, _gpu(M), None, 1.0, 0.0, "f32", 2).cpu().numpy()
+    assert np.array_equal(du, d1)  # the CUDA-core kernel, bit for bit
+    gu = mbl.binding.gram(Av, Av, "f32", 2).cpu().numpy()
+    assert np.all(np.abs(gu - ref_g) <= 8 * 2.0 ** -21 * sg)
+    assert np.all(np.abs(du - ref_u) <= 8 * 2.0 ** -21 * su)
+    # odd leading dimension (p = 63): CUDA cores under engine 2 too
+    A3 = A[:, :63].copy()
+    e1 = mbl.binding.update(_gpu(A3), _gpu(M[:63]), None, 1.0, 0.0, "f32", 1).cpu().numpy()
+    e2 = mbl.binding.update(_gpu(A3), _gpu(M[:63]), None, 1.0, 0.0, "f32", 2).cpu().numpy()
+    assert np.array_equal(e1, e2)
+
+
+@pytest.mark.gpu
 def test_update_engines_agree_on_padded_tiles(mbl):
     """Ragged tails: n not a multiple of the 128-row tile, p not a multiple of the 32-wide K
     chunk or of the 16-column box, q not a multiple of 16 -- the tensor-core result equals
