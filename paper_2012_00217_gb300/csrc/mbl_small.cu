@@ -377,13 +377,18 @@ __device__ void rr_body(int w, int k, int largest, const double *GS, const doubl
     // conditioned (every pivot of the unit-diagonal matrix above chol_tol), C_S = D R^-1,
     // all w directions kept; otherwise SVQB, which drops the nearly dependent directions.
     const T chol_tol = sizeof(T) == sizeof(float) ? (T)1e-3 : (T)1e-8;
-    for (int e = tid; e < w * w; e += nt) T2[e] = A[(e / w) * ld + (e % w)];
-    const bool chol = dev_chol_upper<T>(w, T2, w, chol_tol, &s_flag);
+    // the factor and its inverse in shared memory when the w x w tiles are there (V is free
+    // until the SVQB fallback sets it, A until the projection overwrites it): the column
+    // loops of both are latency chains
+    T *Rm = use_smem ? V : T2, *Ui = use_smem ? A : U;
+    const int ldr = use_smem ? ld : w;
+    for (int e = tid; e < w * w; e += nt) Rm[(e / w) * ldr + (e % w)] = A[(e / w) * ld + (e % w)];
+    const bool chol = dev_chol_upper<T>(w, Rm, ldr, chol_tol, &s_flag);
     if (chol) {
-        dev_tri_inv_upper<T>(w, T2, w, U, w);
+        dev_tri_inv_upper<T>(w, Rm, ldr, Ui, ldr);
         for (int e = tid; e < w * w; e += nt) {
-            const int i = e / w;
-            const double c = dsc[i] * (double)U[e];
+            const int i = e / w, j = e - i * w;
+            const double c = dsc[i] * (double)Ui[i * ldr + j];
             Cs[e] = c;
             Cst[e] = (T)c;
         }
