@@ -314,11 +314,12 @@ struct Solver {
         mark(4);
         MBL_TRY(small_svqb_rr(w, k, largest, gmix, b.G1, b.G2, svqb_tau(), b.coef, b.theta, b.eigw, b.iflags + 1, st));
         mark(5);
-        // 7. updates
-        MBL_TRY(update(b.S, ld3(), w, b.coef, k, k, nullptr, 0, b.Xn, k, n, 1.0, 0.0, 0, st));
-        // the new direction P = [W P] C_WP: FP32 in mixed mode, like W and P themselves
+        // 7. updates.  The new direction P = [W P] C_WP first (FP32 in mixed mode, like W and
+        // P themselves), then X_new = S C = X C_X + P: the [W P] product is formed once, and
+        // the FP64 update of X only spans X's own k columns
         MBL_TRY(update(W(), ld3(), w - k, b.coef + (int64_t)k * k, k, k, nullptr, 0, P(), ld3(), n, 1.0, 0.0, gmix,
                        st));
+        MBL_TRY(update(X(), ld3(), k, b.coef, k, k, P(), ld3(), b.Xn, k, n, 1.0, 1.0, 0, st));
         MBL_TRY(colnorms(P(), ld3(), k, n, b.rn, 1, b.part, st));
         MBL_TRY(scale_cols_inv(P(), ld3(), k, n, b.rn, st));
         MBL_TRY(cholqr_into_x(b.Xn, k));
