@@ -92,7 +92,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *m)
 // ---------------------------------------------------------------------------------
 // Block update D = beta C + alpha A M (A: n x p, M: p x q, C, D: n x q, all FP64 in memory) of
 // the LOBPCG step (Sec. 3.2) with FP32 accuracy on the tensor cores: A and M rounded to FP32
-// and split into two TF32 parts as in the Gram above, D_acc = Ahi Mhi + Ahi Mlo + Alo Mhi per
+// and split into two TF32 parts (file header), D_acc = Ahi Mhi + Ahi Mlo + Alo Mhi per
 // k-step.  Here M of the MMA is a tile of 128 rows of A, N = q (padded to 16), K = p (padded
 // to 16).
 //
